@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the COLA particle-mesh step on GB300.
+
+One "step" is one COLA node (cola_step): CIC deposit, r2c FFT, Green's
+function + ik gradient (fused into the x pass), three c2r FFTs, and the fused
+CIC gather + kick + drift, on 512^3 particles with a 1536^3 FP32 force mesh
+(L = 1536 Mpc/h, 40 linear steps from z = 19; Sec. 2.3 / Table 1 setup with
+PM_grid = 3).  The state comes from cola_ic_2lpt (seeded synthetic Gaussian
+field); the meshes (14.5 GB each) are far larger than L2, so no flush is
+needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload full|small]
+
+Under torchrun each rank advances its own independent realisation (replicas,
+seed 1 + rank): the value is the particle-steps of all ranks divided by the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "full": dict(name="cola_512^3_particles_1536^3_mesh_L1536_40steps", nq=512, ng=1536, box=1536.0),
+    "small": dict(name="cola_32^3_particles_96^3_mesh_L128_40steps", nq=32, ng=96, box=128.0),
+}
+A_INIT, N_NODES = 0.05, 40
+METRIC = "particle-steps/s at 512^3/1536^3"
+UNIT = "particle-steps/s"
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def algorithmic_bytes(name: str, nq: int, ng: int) -> float:
+    """Bytes each kernel must move per launch (one HBM read of its inputs and
+    one write of its outputs; FP32 mesh values, 8-byte fixed-point counts)."""
+    Np = nq**3
+    Mc = ng * ng * (ng // 2 + 1) * 8.0  # half-complex mesh
+    M = ng**3 * 4.0                     # real mesh
+    F = ng**3 * 8.0                     # fixed-point CIC mesh
+    return {
+        "deposit": 12.0 * Np + F,
+        "fft_z_r2c_fix": 2 * F + Mc,
+        "fft_y_fwd": 2 * Mc, "fft_y_inv": 2 * Mc, "fft_x_fwd": 2 * Mc, "fft_x_inv": 2 * Mc,
+        "fft_x_green": 4 * Mc,
+        "fft_z_c2r": Mc + M,
+        "gather_kick_drift": 72.0 * Np + 3 * M,
+    }.get(name, 0.0)
+
+
+def step_reference_bytes(nq: int, ng: int) -> float:
+    """B_ref per PM step: density written, one read+write per 3D transform,
+    the three force meshes read once, 84 bytes per particle."""
+    M = ng**3 * 4.0
+    Mc = ng * ng * (ng // 2 + 1) * 8.0
+    return M + (M + Mc) + 3 * (Mc + M) + 3 * M + 84.0 * nq**3
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1509_04685_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    if j.get("csrc_digest") != csrc_digest():
+        return None
+    k = j.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch_full"])
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running across the timed region."""
+
+    def __init__(self, dev_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(nq=128, ng=384, box=384.0):
+    """The FP64 oracle (as it stands) for one PM step on a bounded sample of the
+    workload: same particle spacing (3 Mpc/h) and PM_grid = 3, 128^3 particles."""
+    import numpy as np
+
+    from oracle import cola as ocola
+    from oracle import cosmology as cm
+    from oracle import lpt
+
+    c = cm.Cosmology()
+    g = cm.Growth(c)
+    tab = cm.step_table(c, cm.time_nodes(A_INIT, 1.0, N_NODES), g)
+    st = lpt.initial_conditions(1, nq, box, cm.LinearPower(c), tab.D1[0], tab.D2[0])
+    t0 = time.perf_counter()
+    ocola.cola_step(st, 20, tab, nq, ng, box)
+    dt = time.perf_counter() - t0
+    return {"value": nq**3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one PM step (node 20) of the FP64 NumPy oracle at {nq}^3 particles on a {ng}^3 mesh, "
+                      f"L={box:g} Mpc/h (same spacing and PM_grid as the workload), {dt:.1f} s; "
+                      "numpy/pocketfft single-threaded"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import cola as ocola
+    from oracle import cosmology as cm
+    from oracle import lpt
+
+    nq, ng, box = 64, 192, 192.0
+    c = cm.Cosmology()
+    tab = cm.step_table(c, cm.time_nodes(A_INIT, 1.0, N_NODES), cm.Growth(c))
+    st = lpt.initial_conditions(1, nq, box, cm.LinearPower(c), tab.D1[0], tab.D2[0])
+    for j in range(args.warmup):
+        ocola.cola_step(st, j % N_NODES, tab, nq, ng, box)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ocola.cola_step(st, (args.warmup + i) % N_NODES, tab, nq, ng, box)
+    dt = time.perf_counter() - t0
+    value = nq**3 * args.steps / dt
+    sample = (f"FP64 NumPy oracle, {nq}^3 particles on a {ng}^3 mesh, L={box:g} Mpc/h (same spacing and "
+              f"PM_grid as the workload), single-threaded")
+    w = WORKLOADS[args.workload]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "nq": w["nq"], "ng": w["ng"], "box": w["box"], "n_steps": N_NODES,
+                   "sample_nq": nq, "sample_ng": ng},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=37)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    import paper_1509_04685_gb300 as C
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = WORKLOADS[args.workload]
+    cfg = C.make_config(w["nq"], w["ng"], w["box"], A_INIT, 1.0, N_NODES)
+    sim = C.Simulation(cfg, device=f"cuda:{local}")
+    sim.ic(seed=1 + rank)
+    for j in range(args.warmup):
+        sim.step(j % N_NODES)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    nk = C.LIB.cola_num_kernel_ids()
+    launches0 = C.cola_launch_count()
+    import ctypes
+    C.LIB.cola_profile_start.argtypes = [ctypes.c_int32]
+    C.LIB.cola_profile_stop.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+    C.LIB.cola_kernel_name.restype = ctypes.c_char_p
+    C.LIB.cola_profile_start(args.steps * 16 + 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(args.steps):
+        sim.step((args.warmup + i) % N_NODES)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = C.cola_launch_count() - launches0
+    kms = (ctypes.c_double * nk)()
+    kcnt = (ctypes.c_int64 * nk)()
+    C.LIB.cola_profile_stop(kms, kcnt, nk)
+    clk = clocks.stop()
+    status = sim.status()
+    if status != 0:
+        raise SystemExit(f"device status {status}: {C.cola_strerror(status)}")
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    per_kernel = {}
+    for i in range(nk):
+        if kcnt[i]:
+            name = C.LIB.cola_kernel_name(i).decode()
+            per_kernel[name] = {"launches": int(kcnt[i]), "ms": kms[i], "share": kms[i] / max(ms, 1e-9)}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dom_avg_ms = per_kernel[dom]["ms"] / per_kernel[dom]["launches"]
+    alg = algorithmic_bytes(dom, w["nq"], w["ng"])
+    peak, peak_kind = peaks()
+    achieved = alg / (dom_avg_ms * 1e-3) / 1e9
+    np_total = w["nq"] ** 3 * world
+    value = np_total * args.steps / (ms * 1e-3)
+    step_ms = ms / args.steps
+    bref = step_reference_bytes(w["nq"], w["ng"])
+
+    # end to end through the public API with host buffers: per step, the state
+    # (d, v, psi1, psi2) comes from pinned host memory and (d, v) go back
+    ke = max(1, args.e2e_steps)
+    hst = [torch.empty_like(x, device="cpu").pin_memory() for x in (sim.d, sim.v, sim.psi1, sim.psi2)]
+    for h, x in zip(hst, (sim.d, sim.v, sim.psi1, sim.psi2)):
+        h.copy_(x)
+    out = [torch.empty_like(x, device="cpu").pin_memory() for x in (sim.d, sim.v)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for i in range(ke):
+        for h, x in zip(hst, (sim.d, sim.v, sim.psi1, sim.psi2)):
+            x.copy_(h, non_blocking=True)
+        sim.step((args.warmup + args.steps + i) % N_NODES)
+        for o, x in zip(out, (sim.d, sim.v)):
+            o.copy_(x, non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = sum(x.numel() * x.element_size() for x in hst)
+    d2h = sum(x.numel() * x.element_size() for x in out)
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "nq": w["nq"], "ng": w["ng"], "box": w["box"], "n_steps": N_NODES,
+                       "z_init": 1 / A_INIT - 1, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (every mesh >> 129 MB); no flush"},
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": {"value": np_total * ke / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": ke},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                         "algorithmic_bytes_per_launch": alg, "traffic": ncu_traffic(dom)},
+            "step_roofline": {"B_ref_bytes": bref, "achieved_GBs": bref / (step_ms * 1e-3) / 1e9,
+                              "frac": bref / (step_ms * 1e-3) / 1e9 / peak},
+            "kernels": per_kernel,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

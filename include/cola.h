@@ -1,0 +1,173 @@
+/*
+ * cola.h -- C ABI of the GB300 COLA particle-mesh library.
+ *
+ * The library advances N-body particles with the COLA method studied in
+ * Izard, Crocce & Fosalba, "ICE-COLA" (arXiv:1509.04685): particles move in the
+ * frame comoving with their 2LPT trajectories (Eq. 1), and only the residual
+ * displacement is integrated in time with particle-mesh forces (Eq. 2), on the
+ * time nodes of Eq. 3.  Sec. 2.2 describes the force as a PM solve on a mesh
+ * PM_grid times finer than the particle grid with one forward and three
+ * inverse FFTs per step; Sec. 2.4 the CIC power-spectrum estimator.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: lengths in Mpc/h, time in 1/H0; momenta p = a^2 dx/dt.
+ * Particles: Np = nq^3, index p = (i*nq + j)*nq + k (Lagrangian C order, z
+ *   fastest).  Particle fields are SoA float arrays of 3*Np values: component c
+ *   of particle p at [c*Np + p].  Lagrangian position q = (i,j,k)*L/nq + L/(2 ng)
+ *   (the lattice sits at force-mesh cell midpoints); position x = q + d.
+ * Memory: every pointer argument is a DEVICE pointer unless stated otherwise.
+ *   All memory is owned by the caller: the library never allocates.  The
+ *   workspace (size from cola_workspace_size) holds the FP64 step tables, the
+ *   FFT twiddles and every mesh; its contents between calls are private.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call only enqueues work and returns; results are ready when
+ *   the stream is.  Calls on one workspace must not overlap in time.
+ * Errors: host-side argument errors are returned immediately (negative codes,
+ *   see cola_strerror).  Errors a kernel detects (non-finite input, a bounded
+ *   wait that gave up) are latched in a status word inside the workspace and
+ *   returned by cola_status.
+ */
+#ifndef COLA_GB300_H
+#define COLA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COLA_OK 0
+#define COLA_EINVAL (-1)            /* bad argument (NULL pointer, size, range) */
+#define COLA_EWORKSPACE (-2)        /* workspace smaller than cola_workspace_size */
+#define COLA_EUNSUPPORTED_SIZE (-3) /* a mesh side with a prime factor > 5, odd, or too large */
+#define COLA_ECUDA (-4)             /* a CUDA launch or runtime call failed */
+#define COLA_ETIMEOUT (-5)          /* a bounded device-side wait gave up */
+#define COLA_ENONFINITE (-6)        /* a kernel met a NaN/Inf in its input */
+
+#define COLA_SAMPLING_LINEAR 0 /* Eq. 3 with f(a) = a (the paper's choice, Sec. 4.2) */
+#define COLA_SAMPLING_LOG 1    /* f(a) = ln a */
+#define COLA_SAMPLING_POW 2    /* f(a) = a^p, p = sampling_p */
+
+#define COLA_FLAG_PM_ONLY 1u /* App. B: plain PM, no LPT frame (v holds the full momentum) */
+
+#define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.4) */
+#define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.4) */
+
+/* Flat LCDM parameters (Sec. 2.1, MICE-GC: 0.25, 0.75, 0.044, 0.7, 0.8, 0.95). */
+typedef struct cola_cosmology {
+    double omega_m, omega_l, omega_b, h, sigma8, n_s;
+    double t_cmb; /* K, used by the Eisenstein & Hu no-wiggle transfer function */
+} cola_cosmology;
+
+/* One simulation (Table 1's code parameters). */
+typedef struct cola_config {
+    int32_t nq;         /* particles per side (even) */
+    int32_t ng;         /* force mesh cells per side: PM_grid * nq (Sec. 2.2); even, 2^a 3^b 5^c */
+    double box;         /* L in Mpc/h */
+    double a_init;      /* a_i = 1/(1+z_i) (Sec. 4.3) */
+    double a_final;     /* a_f (1 in the paper) */
+    int32_t n_steps;    /* number of time nodes n of Eq. 3 = force evaluations */
+    int32_t sampling;   /* COLA_SAMPLING_* */
+    double sampling_p;  /* exponent for COLA_SAMPLING_POW */
+    uint32_t flags;     /* COLA_FLAG_* */
+    cola_cosmology cosmo;
+} cola_config;
+
+/* Particle state: four SoA float[3*Np] device arrays.
+ * d: displacement x - q;  v: residual momentum p - p_LPT (Eq. 1);
+ * psi1, psi2: first- and second-order LPT displacements at D1 = 1. */
+typedef struct cola_state {
+    float* d;
+    float* v;
+    float* psi1;
+    float* psi2;
+} cola_state;
+
+/* Bytes of workspace that every call with this configuration needs (the
+ * largest of the step, the 2LPT set-up and a P(k) on a mesh of side <= ng). */
+int cola_workspace_size(const cola_config* cfg, size_t* bytes);
+
+/* Fill the workspace's FP64 tables: growth factors D1, D2 (growth ODEs), the
+ * per-node kick/drift integrals of the KDK scheme for Eq. 2 and the FFT
+ * twiddles.  Required once per workspace before cola_step / cola_pm_force;
+ * cola_ic_2lpt calls it itself.  Also clears the status word. */
+int cola_init(const cola_config* cfg, void* ws, size_t ws_bytes, void* stream);
+
+/* 2LPT initial conditions (Sec. 2.2: Gaussian random field + 2LPT).  White
+ * noise from Philox-4x32-10 keyed by `seed` (the same field for every run with
+ * that seed, Sec. 2.3), scaled by the Eisenstein-Hu no-wiggle P(k) normalised
+ * to sigma8; writes psi1, psi2, d = D1(a_i) psi1 + D2(a_i) psi2 and v = 0.
+ * Runs cola_init first. */
+int cola_ic_2lpt(const cola_config* cfg, uint64_t seed, cola_state* st, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* Particle-mesh force at scale factor `a` (Eq. 2 right-hand side, -grad Phi
+ * with lap Phi = 3/2 Om/a delta): CIC deposit, r2c FFT, Green's function and
+ * ik gradient, three c2r FFTs, CIC gather.  `force` is SoA float[3*Np]. */
+int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float* force, void* ws,
+                  size_t ws_bytes, void* stream);
+
+/* One COLA node j (0 <= j < n_steps): force at a_j, kick of the residual
+ * momentum by the LPT-frame acceleration F - c1 psi1 - c2 psi2, then (j < n-1)
+ * drift of d by the residual momentum plus the D1/D2 increments.  After node
+ * j < n-1 the positions are at a_{j+1}; after the last node v is at a_f. */
+int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes,
+              void* stream);
+
+/* Matter power spectrum (Sec. 2.4) of the state on a CIC mesh of side ng_pk
+ * (2 <= ng_pk <= ng, even, 2^a 3^b 5^c).  `node` is the time node the
+ * positions sit at; if a_out differs from a_node the positions are first
+ * drifted to a_out on the fly with the state's momentum (no force
+ * evaluation).  k, pk, nmodes are DEVICE float64 arrays of nbins = ng_pk/2:
+ * bin i holds modes with (i+1/2)^2 > |n|^2 > (i-1/2)^2 (i = 1..ng_pk/2). */
+int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t node, double a_out,
+                        int32_t ng_pk, int32_t flags, double* k, double* pk, double* nmodes,
+                        int32_t nbins, void* ws, size_t ws_bytes, void* stream);
+
+/* Density contrast delta = rho (ng/nq)^3 - 1 of the state on the force mesh,
+ * written unpadded as float[ng^3] (C order).  The deposit is deterministic
+ * (fixed-point, 2^40 per particle). */
+int cola_density(const cola_config* cfg, const cola_state* st, float* delta, void* ws,
+                 size_t ws_bytes, void* stream);
+
+/* FP64 step table as computed on the device: n_steps rows of 12 doubles
+ * (a, green, c1, c2, kick, drift, dD1, dD2, D1, D2, dD1/da, dD2/da), copied
+ * to the DEVICE array `out`. */
+int cola_step_table(const cola_config* cfg, double* out, void* ws, size_t ws_bytes, void* stream);
+
+/* In-place 3D FFTs of an n^3 mesh stored with half-complex row pitch
+ * cola_fft_pitch(n) complex values (real rows padded to 2*pitch floats).
+ * r2c is unnormalised (exp(-i k x)); c2r is the unnormalised inverse (the
+ * caller divides by n^3). Uses the workspace of any config with ng >= n. */
+int32_t cola_fft_pitch(int32_t n);
+int cola_fft3d_r2c(int32_t n, float* data, void* ws, size_t ws_bytes, void* stream);
+int cola_fft3d_c2r(int32_t n, float* data, void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronise `stream`, return the latched device status (COLA_OK or a
+ * negative code) and clear it. */
+int cola_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Number of kernels this library launched since load (a counter the host
+ * side increments per launch). */
+uint64_t cola_launch_count(void);
+
+/* Per-kernel timing (tracing): between cola_profile_start and
+ * cola_profile_stop every kernel launch of the library is bracketed by CUDA
+ * events on its own stream (at most max_records launches are recorded).
+ * cola_profile_stop synchronises on the events and returns, per kernel id,
+ * the summed milliseconds and the launch count (arrays of at least
+ * cola_num_kernel_ids() entries, HOST memory). */
+int cola_profile_start(int32_t max_records);
+int cola_profile_stop(double* ms, int64_t* launches, int32_t nkernels);
+int32_t cola_num_kernel_ids(void);
+const char* cola_kernel_name(int32_t id);
+
+const char* cola_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLA_GB300_H */

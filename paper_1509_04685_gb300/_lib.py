@@ -1,0 +1,182 @@
+"""ctypes binding of libcola_gb300.so (include/cola.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Tensors are passed by device pointer (``tensor.data_ptr()``); the
+stream is the caller's current torch stream unless given.  There is no CPU
+fallback: if the library is missing or fails to load, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcola_gb300.so")
+
+COLA_OK = 0
+ERRORS = {-1: "COLA_EINVAL", -2: "COLA_EWORKSPACE", -3: "COLA_EUNSUPPORTED_SIZE", -4: "COLA_ECUDA",
+          -5: "COLA_ETIMEOUT", -6: "COLA_ENONFINITE"}
+SAMPLING_LINEAR, SAMPLING_LOG, SAMPLING_POW = 0, 1, 2
+FLAG_PM_ONLY = 1
+PK_DECONV_CIC, PK_ALIAS_JING = 1, 2
+TABLE_COLUMNS = ("a", "green", "c1", "c2", "kick", "drift", "dD1", "dD2", "D1", "D2", "dD1da", "dD2da")
+
+
+class cola_cosmology(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double), ("omega_b", ctypes.c_double),
+                ("h", ctypes.c_double), ("sigma8", ctypes.c_double), ("n_s", ctypes.c_double),
+                ("t_cmb", ctypes.c_double)]
+
+
+class cola_config(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32), ("ng", ctypes.c_int32), ("box", ctypes.c_double),
+                ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("n_steps", ctypes.c_int32),
+                ("sampling", ctypes.c_int32), ("sampling_p", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("cosmo", cola_cosmology)]
+
+
+class cola_state(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_void_p), ("v", ctypes.c_void_p), ("psi1", ctypes.c_void_p),
+                ("psi2", ctypes.c_void_p)]
+
+
+class ColaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({_strerror(code)})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"COLA CUDA library not built ({LIB_PATH}); run paper_1509_04685_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, sz, i32, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double
+    cfgp, stp = ctypes.POINTER(cola_config), ctypes.POINTER(cola_state)
+    sigs = {
+        "cola_workspace_size": ([cfgp, ctypes.POINTER(sz)], ctypes.c_int),
+        "cola_init": ([cfgp, vp, sz, vp], ctypes.c_int),
+        "cola_ic_2lpt": ([cfgp, ctypes.c_uint64, stp, vp, sz, vp], ctypes.c_int),
+        "cola_pm_force": ([cfgp, stp, dbl, vp, vp, sz, vp], ctypes.c_int),
+        "cola_step": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
+        "cola_power_spectrum": ([cfgp, stp, i32, dbl, i32, i32, vp, vp, vp, i32, vp, sz, vp], ctypes.c_int),
+        "cola_density": ([cfgp, stp, vp, vp, sz, vp], ctypes.c_int),
+        "cola_step_table": ([cfgp, vp, vp, sz, vp], ctypes.c_int),
+        "cola_fft_pitch": ([i32], i32),
+        "cola_fft3d_r2c": ([i32, vp, vp, sz, vp], ctypes.c_int),
+        "cola_fft3d_c2r": ([i32, vp, vp, sz, vp], ctypes.c_int),
+        "cola_status": ([vp, sz, vp], ctypes.c_int),
+        "cola_launch_count": ([], ctypes.c_uint64),
+        "cola_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _strerror(code: int) -> str:
+    return LIB.cola_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != COLA_OK:
+        raise ColaError(rc, what)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def make_config(nq: int, ng: int, box: float, a_init: float, a_final: float = 1.0, n_steps: int = 40,
+                sampling: int = SAMPLING_LINEAR, sampling_p: float = 1.0, flags: int = 0,
+                omega_m=0.25, omega_l=0.75, omega_b=0.044, h=0.7, sigma8=0.8, n_s=0.95, t_cmb=2.7255):
+    cosmo = cola_cosmology(omega_m, omega_l, omega_b, h, sigma8, n_s, t_cmb)
+    return cola_config(nq, ng, box, a_init, a_final, n_steps, sampling, sampling_p, flags, cosmo)
+
+
+def make_state(d, v=None, psi1=None, psi2=None) -> cola_state:
+    return cola_state(_ptr(d), _ptr(v), _ptr(psi1), _ptr(psi2))
+
+
+def cola_workspace_size(cfg: cola_config) -> int:
+    out = ctypes.c_size_t(0)
+    _check(LIB.cola_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "cola_workspace_size")
+    return out.value
+
+
+def cola_init(cfg, ws, stream=None):
+    _check(LIB.cola_init(ctypes.byref(cfg), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "cola_init")
+
+
+def cola_ic_2lpt(cfg, seed: int, st: cola_state, ws, stream=None):
+    _check(LIB.cola_ic_2lpt(ctypes.byref(cfg), seed, ctypes.byref(st), _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream(stream)), "cola_ic_2lpt")
+
+
+def cola_pm_force(cfg, st: cola_state, a: float, force, ws, stream=None):
+    _check(LIB.cola_pm_force(ctypes.byref(cfg), ctypes.byref(st), a, _ptr(force), _ptr(ws),
+                             ws.numel() * ws.element_size(), _stream(stream)), "cola_pm_force")
+
+
+def cola_step(cfg, st: cola_state, step: int, ws, stream=None):
+    _check(LIB.cola_step(ctypes.byref(cfg), ctypes.byref(st), step, _ptr(ws), ws.numel() * ws.element_size(),
+                         _stream(stream)), "cola_step")
+
+
+def cola_power_spectrum(cfg, st: cola_state, node: int, a_out: float, ng_pk: int, flags: int, k, pk, nmodes, ws,
+                        stream=None):
+    _check(LIB.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), node, a_out, ng_pk, flags, _ptr(k), _ptr(pk),
+                                   _ptr(nmodes), ng_pk // 2, _ptr(ws), ws.numel() * ws.element_size(),
+                                   _stream(stream)), "cola_power_spectrum")
+
+
+def cola_density(cfg, st: cola_state, delta, ws, stream=None):
+    _check(LIB.cola_density(ctypes.byref(cfg), ctypes.byref(st), _ptr(delta), _ptr(ws),
+                            ws.numel() * ws.element_size(), _stream(stream)), "cola_density")
+
+
+def cola_step_table(cfg, out, ws, stream=None):
+    _check(LIB.cola_step_table(ctypes.byref(cfg), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream)), "cola_step_table")
+
+
+def cola_fft_pitch(n: int) -> int:
+    return LIB.cola_fft_pitch(n)
+
+
+def cola_fft3d_r2c(n: int, data, ws, stream=None):
+    _check(LIB.cola_fft3d_r2c(n, _ptr(data), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "cola_fft3d_r2c")
+
+
+def cola_fft3d_c2r(n: int, data, ws, stream=None):
+    _check(LIB.cola_fft3d_c2r(n, _ptr(data), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "cola_fft3d_c2r")
+
+
+def cola_status(ws, stream=None) -> int:
+    return LIB.cola_status(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def cola_launch_count() -> int:
+    return LIB.cola_launch_count()
+
+
+def cola_strerror(code: int) -> str:
+    return _strerror(code)

@@ -1,0 +1,307 @@
+// C ABI entry points (include/cola.h): argument checking, workspace layout and
+// the sequencing of the kernels of each call.  No allocation happens here:
+// every buffer lives in the caller's workspace or state arrays.
+#include <cmath>
+#include <cstring>
+
+#include "cola_common.cuh"
+
+namespace cola {
+
+static bool factorable(int n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+static bool mesh_ok(int n) { return n >= 4 && n % 2 == 0 && n <= kMaxFft && factorable(n) && factorable(n / 2); }
+
+static int check_config(const cola_config* c) {
+    if (!c) return COLA_EINVAL;
+    if (!mesh_ok(c->nq) || !mesh_ok(c->ng)) return COLA_EUNSUPPORTED_SIZE;
+    if (!(c->box > 0.0) || !(c->a_init > 0.0) || !(c->a_final > c->a_init) || !(c->a_final <= 1.0))
+        return COLA_EINVAL;
+    if (c->n_steps < 2 || c->n_steps > kMaxSteps) return COLA_EINVAL;
+    if (c->sampling < COLA_SAMPLING_LINEAR || c->sampling > COLA_SAMPLING_POW) return COLA_EINVAL;
+    if (c->sampling == COLA_SAMPLING_POW && !(c->sampling_p > 0.0)) return COLA_EINVAL;
+    const cola_cosmology& k = c->cosmo;
+    if (!(k.omega_m > 0.0) || !(k.h > 0.0) || !(k.sigma8 > 0.0) || !(k.omega_b >= 0.0) || !(k.t_cmb > 0.0))
+        return COLA_EINVAL;
+    return COLA_OK;
+}
+
+bool layout_for(const cola_config* cfg, Layout* L) {
+    const int ng = cfg->ng, nq = cfg->nq;
+    const size_t Mg = mesh_bytes(ng), Mq = mesh_bytes(nq);
+    L->dep = align_up(kHdrBytes, 4096);
+    L->mk = align_up(L->dep + (size_t)ng * ng * ng * 8, 4096);
+    for (int j = 0; j < 3; ++j) L->force[j] = align_up(L->mk + (j + 1) * Mg, 4096);
+    L->ic = L->dep;
+    L->pk_part = L->force[0];
+    size_t end = L->force[2] + Mg;
+    size_t ic_end = L->ic + 7 * Mq;
+    size_t pk_end = L->pk_part + power_partial_bytes(ng / 2);
+    if (ic_end > end) end = ic_end;
+    if (pk_end > end) end = pk_end;
+    L->total = align_up(end, 4096);
+    return true;
+}
+
+static int check_ws(const cola_config* cfg, void* ws, size_t ws_bytes, Layout* L) {
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    layout_for(cfg, L);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return COLA_EINVAL;
+    if (ws_bytes < L->total) return COLA_EWORKSPACE;
+    return COLA_OK;
+}
+
+static bool state_ok(const cola_state* st, bool need_all) {
+    if (!st || !st->d) return false;
+    if (need_all && (!st->v || !st->psi1 || !st->psi2)) return false;
+    return true;
+}
+
+static double host_node_a(const cola_config* c, int j) {
+    const double t = (double)j / (double)(c->n_steps - 1);
+    const double ai = c->a_init, af = c->a_final;
+    if (c->sampling == COLA_SAMPLING_LOG) return std::exp(std::log(ai) + t * (std::log(af) - std::log(ai)));
+    if (c->sampling == COLA_SAMPLING_POW) {
+        const double p = c->sampling_p;
+        return std::pow(std::pow(ai, p) + t * (std::pow(af, p) - std::pow(ai, p)), 1.0 / p);
+    }
+    return ai + t * (af - ai);
+}
+
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// deposit + forward z, y passes + fused x/Green pass + inverse y, z passes:
+// leaves the three force components in the real views of force[0..2].
+static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
+                          cudaStream_t s) {
+    const int ng = cfg->ng, nq = cfg->nq;
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+    float2* mk = reinterpret_cast<float2*>(wsp(ws, L.mk));
+    float2* f[3];
+    for (int j = 0; j < 3; ++j) f[j] = reinterpret_cast<float2*>(wsp(ws, L.force[j]));
+    const float2* tw = twiddle_ptr(ws, kTwMesh);
+    const double ratio = (double)ng / (double)nq;
+    const float scale = (float)(ratio * ratio * ratio / 1099511627776.0);
+    const double ng3 = (double)ng * ng * ng;
+    int rc;
+    if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws), s)))
+        return rc;
+    if ((rc = fft_z_r2c(dep, mk, ng, scale, tw, s))) return rc;
+    if ((rc = fft_strided(mk, ng, 1, -1, tw, s))) return rc;
+    if ((rc = fft_x_green(mk, f[0], f[1], f[2], ng, (float)(green / ng3),
+                          (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s)))
+        return rc;
+    for (int j = 0; j < 3; ++j) {
+        if ((rc = fft_strided(f[j], ng, 1, +1, tw, s))) return rc;
+        if ((rc = fft_z_c2r(f[j], ng, tw, s, nullptr, 0, 1.f))) return rc;
+    }
+    return COLA_OK;
+}
+
+static const float2* twiddles_for(int n, const cola_config* cfg, void* ws, cudaStream_t s, int* rc) {
+    if (cfg && n == cfg->ng) return twiddle_ptr(ws, kTwMesh);
+    if (cfg && n == cfg->nq) return twiddle_ptr(ws, kTwLagr);
+    float2* tw = twiddle_ptr(ws, kTwScratch);
+    *rc = launch_twiddles(tw, n, s);
+    return tw;
+}
+
+}  // namespace cola
+
+using namespace cola;
+
+extern "C" {
+
+int cola_workspace_size(const cola_config* cfg, size_t* bytes) {
+    if (!bytes) return COLA_EINVAL;
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    Layout L;
+    layout_for(cfg, &L);
+    *bytes = L.total;
+    return COLA_OK;
+}
+
+int cola_init(const cola_config* cfg, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    if (cudaMemsetAsync(ws, 0, kHdrBytes, s) != cudaSuccess) return COLA_ECUDA;
+    if (cudaMemsetAsync(wsp(ws, L.dep), 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess)
+        return COLA_ECUDA;
+    if ((rc = launch_twiddles(twiddle_ptr(ws, kTwMesh), cfg->ng, s))) return rc;
+    if ((rc = launch_twiddles(twiddle_ptr(ws, kTwLagr), cfg->nq, s))) return rc;
+    return launch_tables(cfg, table_ptr(ws), s);
+}
+
+int cola_ic_2lpt(const cola_config* cfg, uint64_t seed, cola_state* st, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, true)) return COLA_EINVAL;
+    if ((rc = cola_init(cfg, ws, ws_bytes, stream))) return rc;
+    cudaStream_t s = S(stream);
+    if ((rc = launch_ic(cfg, seed, *st, ws, L, s))) return rc;
+    // the 2LPT scratch aliases the fixed-point mesh, which must be zero between calls
+    if (cudaMemsetAsync(wsp(ws, L.dep), 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess)
+        return COLA_ECUDA;
+    return COLA_OK;
+}
+
+int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float* force, void* ws, size_t ws_bytes,
+                  void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, false) || !force || !(a > 0.0)) return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    const double green = 1.5 * cfg->cosmo.omega_m / a;
+    if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
+    return launch_gather(reinterpret_cast<float2*>(wsp(ws, L.force[0])),
+                         reinterpret_cast<float2*>(wsp(ws, L.force[1])),
+                         reinterpret_cast<float2*>(wsp(ws, L.force[2])), st->d, force, cfg->nq, cfg->ng, cfg->box, s);
+}
+
+int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, true) || step < 0 || step >= cfg->n_steps) return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
+    if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
+    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.force[0])),
+                                    reinterpret_cast<float2*>(wsp(ws, L.force[1])),
+                                    reinterpret_cast<float2*>(wsp(ws, L.force[2])), *st,
+                                    table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
+                                    step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
+                                    status_ptr(ws), s);
+}
+
+int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t node, double a_out, int32_t ng_pk,
+                        int32_t flags, double* k, double* pk, double* nmodes, int32_t nbins, void* ws,
+                        size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, false) || !k || !pk || !nmodes) return COLA_EINVAL;
+    if (!mesh_ok(ng_pk) || ng_pk > cfg->ng) return COLA_EUNSUPPORTED_SIZE;
+    if (nbins != ng_pk / 2 || node < 0 || node >= cfg->n_steps || (flags & ~3)) return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    const double a_node = host_node_a(cfg, node);
+    const double* snap = nullptr;
+    if (std::fabs(a_out - a_node) > 1e-12 * a_node) {
+        if (!(a_out > 0.0) || !state_ok(st, true)) return COLA_EINVAL;
+        double* sp = reinterpret_cast<double*>(wsp(ws, kHdrSnap));
+        if ((rc = launch_snapshot_coeffs(cfg, a_node, a_out, sp, s))) return rc;
+        snap = sp;
+    }
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+    float2* mk = reinterpret_cast<float2*>(wsp(ws, L.mk));
+    const float2* tw = twiddles_for(ng_pk, cfg, ws, s, &rc);
+    if (rc) return rc;
+    const double ratio = (double)ng_pk / (double)cfg->nq;
+    if ((rc = launch_deposit_ex(st->d, st->v, st->psi1, st->psi2, dep, cfg->nq, ng_pk, cfg->box, snap,
+                                status_ptr(ws), s)))
+        return rc;
+    if ((rc = fft_z_r2c(dep, mk, ng_pk, (float)(ratio * ratio * ratio / 1099511627776.0), tw, s))) return rc;
+    if ((rc = fft_strided(mk, ng_pk, 1, -1, tw, s))) return rc;
+    if ((rc = fft_strided(mk, ng_pk, 0, -1, tw, s))) return rc;
+    return launch_power(mk, ng_pk, cfg->box, flags, reinterpret_cast<double*>(wsp(ws, L.pk_part)), k, pk, nmodes,
+                        nbins, s);
+}
+
+int cola_density(const cola_config* cfg, const cola_state* st, float* delta, void* ws, size_t ws_bytes,
+                 void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, false) || !delta) return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+    if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, cfg->nq, cfg->ng, cfg->box, nullptr,
+                                status_ptr(ws), s)))
+        return rc;
+    const double ratio = (double)cfg->ng / (double)cfg->nq;
+    return launch_fix_to_delta(dep, delta, cfg->ng, (float)(ratio * ratio * ratio / 1099511627776.0), s);
+}
+
+int cola_step_table(const cola_config* cfg, double* out, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!out) return COLA_EINVAL;
+    return cudaMemcpyAsync(out, table_ptr(ws), (size_t)cfg->n_steps * kTableCols * sizeof(double),
+                           cudaMemcpyDeviceToDevice, S(stream)) == cudaSuccess
+               ? COLA_OK
+               : COLA_ECUDA;
+}
+
+int32_t cola_fft_pitch(int32_t n) { return n > 0 ? fft_pitch(n) : 0; }
+
+static int fft3d_common(int32_t n, float* data, void* ws, size_t ws_bytes) {
+    if (!mesh_ok(n)) return COLA_EUNSUPPORTED_SIZE;
+    if (!data || !ws || ws_bytes < kHdrBytes || (reinterpret_cast<uintptr_t>(ws) & 255) ||
+        (reinterpret_cast<uintptr_t>(data) & 15))
+        return COLA_EINVAL;
+    return COLA_OK;
+}
+
+int cola_fft3d_r2c(int32_t n, float* data, void* ws, size_t ws_bytes, void* stream) {
+    int rc = fft3d_common(n, data, ws, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const float2* tw = twiddles_for(n, nullptr, ws, s, &rc);
+    if (rc) return rc;
+    float2* c = reinterpret_cast<float2*>(data);
+    if ((rc = fft_z_r2c(nullptr, c, n, 0.f, tw, s))) return rc;
+    if ((rc = fft_strided(c, n, 1, -1, tw, s))) return rc;
+    return fft_strided(c, n, 0, -1, tw, s);
+}
+
+int cola_fft3d_c2r(int32_t n, float* data, void* ws, size_t ws_bytes, void* stream) {
+    int rc = fft3d_common(n, data, ws, ws_bytes);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const float2* tw = twiddles_for(n, nullptr, ws, s, &rc);
+    if (rc) return rc;
+    float2* c = reinterpret_cast<float2*>(data);
+    if ((rc = fft_strided(c, n, 0, +1, tw, s))) return rc;
+    if ((rc = fft_strided(c, n, 1, +1, tw, s))) return rc;
+    return fft_z_c2r(c, n, tw, s, nullptr, 0, 1.f);
+}
+
+int cola_status(void* ws, size_t ws_bytes, void* stream) {
+    if (!ws || ws_bytes < kHdrBytes) return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    int host = 0;
+    if (cudaMemcpyAsync(&host, status_ptr(ws), sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return COLA_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return COLA_ECUDA;
+    if (host != 0 && cudaMemsetAsync(status_ptr(ws), 0, sizeof(int), s) != cudaSuccess) return COLA_ECUDA;
+    return host;
+}
+
+uint64_t cola_launch_count(void) { return g_launches; }
+
+const char* cola_strerror(int code) {
+    switch (code) {
+        case COLA_OK: return "ok";
+        case COLA_EINVAL: return "invalid argument";
+        case COLA_EWORKSPACE: return "workspace too small";
+        case COLA_EUNSUPPORTED_SIZE: return "unsupported mesh size (must be even, <= 4096, factors 2, 3, 5)";
+        case COLA_ECUDA: return "CUDA launch or runtime error";
+        case COLA_ETIMEOUT: return "a bounded device wait gave up";
+        case COLA_ENONFINITE: return "non-finite or out-of-range particle data";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

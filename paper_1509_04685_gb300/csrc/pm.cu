@@ -1,0 +1,235 @@
+// Particle side of the PM step (Sec. 2.2): CIC deposit onto the force mesh and
+// the fused CIC gather + COLA kick + drift in the frame comoving with the
+// 2LPT trajectories (Eqs. 1-2).
+//
+// Particle p = (i*nq + j)*nq + k sits at mesh coordinate
+//   u = (i, j, k) * ng/nq + 1/2 + d * ng/L      (periodic)
+// The Lagrangian part is formed exactly in integers, (i*2ng + nq)/(2nq), and
+// only the small displacement term is FP32, so the CIC fraction keeps FP32
+// precision for any mesh size.
+//
+// Deposit determinism: each particle's eight CIC weights are turned into
+// unsigned 64-bit fixed point with 2^40 per particle (the largest corner takes
+// the remainder so the eight sum to exactly 2^40) and added with integer
+// atomics, which commute: the mesh is bit-identical run to run.
+#include "cola_common.cuh"
+
+namespace cola {
+
+constexpr float kFix = 1099511627776.0f;  // 2^40
+constexpr unsigned long long kFixU = 1ull << 40;
+
+struct Cic {
+    int c0[3];    // lower corner cell (wrapped)
+    int c1[3];    // upper corner cell (wrapped)
+    float f[3];   // fraction towards the upper corner
+};
+
+__device__ __forceinline__ bool particle_cic(long long p, int nq, int ng, float inv_cell, const float dx[3],
+                                             Cic& c) {
+    const long long nq2 = (long long)nq * nq;
+    const int idx[3] = {(int)(p / nq2), (int)((p / nq) % nq), (int)(p % nq)};
+    const long long den = 2ll * nq;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long num = (long long)idx[a] * 2 * ng + nq;
+        const long long base = num / den;
+        const float frac0 = (float)(num - base * den) / (float)den;
+        const float t = frac0 + dx[a] * inv_cell;
+        if (!(fabsf(t) < 1.0e7f)) return false;  // NaN, Inf or absurd displacement
+        const float fl = floorf(t);
+        c.f[a] = t - fl;
+        long long cell = (base + (long long)fl) % ng;
+        if (cell < 0) cell += ng;
+        c.c0[a] = (int)cell;
+        c.c1[a] = (cell + 1 == ng) ? 0 : (int)cell + 1;
+    }
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// deposit (optionally drifting to an output time on the fly:
+// d_out = d + dr v + dD1 psi1 + dD2 psi2, coefficients in snap[0..2])
+// --------------------------------------------------------------------------
+template <bool SNAP>
+__global__ void k_deposit(const float* __restrict__ d, const float* __restrict__ v, const float* __restrict__ psi1,
+                          const float* __restrict__ psi2, unsigned long long* __restrict__ dep, int nq, int ng,
+                          float inv_cell, long long np, const double* __restrict__ snap, int* status) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float dx[3];
+    float dr = 0.f, d1 = 0.f, d2 = 0.f;
+    if (SNAP) {
+        dr = (float)snap[0];
+        d1 = (float)snap[1];
+        d2 = (float)snap[2];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dx[a] = d[a * np + p];
+        if (SNAP) dx[a] += dr * v[a * np + p] + d1 * psi1[a * np + p] + d2 * psi2[a * np + p];
+    }
+    Cic c;
+    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+        set_status(status, COLA_ENONFINITE);
+        return;
+    }
+    const float wx[2] = {1.f - c.f[0], c.f[0]};
+    const float wy[2] = {1.f - c.f[1], c.f[1]};
+    const float wz[2] = {1.f - c.f[2], c.f[2]};
+    const int mx = c.f[0] >= 0.5f, my = c.f[1] >= 0.5f, mz = c.f[2] >= 0.5f;
+    const int ix[2] = {c.c0[0], c.c1[0]};
+    const int iy[2] = {c.c0[1], c.c1[1]};
+    const int iz[2] = {c.c0[2], c.c1[2]};
+    unsigned long long rest = kFixU;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (a == mx && b == my && e == mz) continue;
+                const unsigned long long w = __float2ull_rn(wx[a] * wy[b] * wz[e] * kFix);
+                rest -= w;
+                const long long cell = ((long long)ix[a] * ng + iy[b]) * ng + iz[e];
+                atomicAdd(dep + cell, w);
+            }
+    const long long cell = ((long long)ix[mx] * ng + iy[my]) * ng + iz[mz];
+    atomicAdd(dep + cell, rest);
+}
+
+int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
+                      int nq, int ng, double box, const double* snap, int* status, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const int T = 256;
+    const unsigned grid = (unsigned)((np + T - 1) / T);
+    const float inv_cell = (float)((double)ng / box);
+    ProfScope ps(kKDeposit, s);
+    if (snap)
+        k_deposit<true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status);
+    else
+        k_deposit<false><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, nullptr, status);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// CIC interpolation of the three force meshes (real view, row pitch P2 floats)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void gather3(const float* __restrict__ f0, const float* __restrict__ f1,
+                                        const float* __restrict__ f2, int ng, long long P2, const Cic& c,
+                                        float F[3]) {
+    F[0] = F[1] = F[2] = 0.f;
+    const int ix[2] = {c.c0[0], c.c1[0]};
+    const int iy[2] = {c.c0[1], c.c1[1]};
+    const int iz[2] = {c.c0[2], c.c1[2]};
+    const float wx[2] = {1.f - c.f[0], c.f[0]};
+    const float wy[2] = {1.f - c.f[1], c.f[1]};
+    const float wz[2] = {1.f - c.f[2], c.f[2]};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const long long row = ((long long)ix[a] * ng + iy[b]) * P2;
+            const float wab = wx[a] * wy[b];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float w = wab * wz[e];
+                const long long q = row + iz[e];
+                F[0] += w * __ldg(f0 + q);
+                F[1] += w * __ldg(f1 + q);
+                F[2] += w * __ldg(f2 + q);
+            }
+        }
+}
+
+__global__ void k_gather(const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
+                         const float* __restrict__ d, float* __restrict__ out, int nq, int ng, long long P2,
+                         float inv_cell, long long np) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float dx[3] = {d[p], d[np + p], d[2 * np + p]};
+    Cic c;
+    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+        out[p] = out[np + p] = out[2 * np + p] = __int_as_float(0x7fc00000);
+        return;
+    }
+    float F[3];
+    gather3(f0, f1, f2, ng, P2, c, F);
+    out[p] = F[0];
+    out[np + p] = F[1];
+    out[2 * np + p] = F[2];
+}
+
+int launch_gather(const float2* f0, const float2* f1, const float2* f2, const float* d, float* out, int nq, int ng,
+                  double box, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const int T = 256;
+    ProfScope ps(kKGather, s);
+    k_gather<<<(unsigned)((np + T - 1) / T), T, 0, s>>>((const float*)f0, (const float*)f1, (const float*)f2, d, out,
+                                                         nq, ng, 2ll * fft_pitch(ng), (float)((double)ng / box), np);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// fused gather + kick + drift of node j.  row = FP64 table row:
+// (a, green, c1, c2, kick, drift, dD1, dD2, ...), each rounded once to FP32.
+//   A = F - c1 psi1 - c2 psi2;  v += kick A;  (not last) d += drift v + dD1 psi1 + dD2 psi2
+// PM-only (App. B): A = F, d += drift v.
+// --------------------------------------------------------------------------
+__global__ void k_gather_kick_drift(const float* __restrict__ f0, const float* __restrict__ f1,
+                                    const float* __restrict__ f2, float* __restrict__ d, float* __restrict__ v,
+                                    const float* __restrict__ psi1, const float* __restrict__ psi2,
+                                    const double* __restrict__ row, int nq, int ng, long long P2, float inv_cell,
+                                    long long np, int last, int pm_only, int* status) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const float c1 = (float)row[2], c2 = (float)row[3], kick = (float)row[4];
+    const float drift = (float)row[5], dD1 = (float)row[6], dD2 = (float)row[7];
+    float dx[3] = {d[p], d[np + p], d[2 * np + p]};
+    Cic c;
+    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+        set_status(status, COLA_ENONFINITE);
+        return;
+    }
+    float F[3];
+    gather3(f0, f1, f2, ng, P2, c, F);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long q = a * np + p;
+        const float s1 = psi1[q], s2 = psi2[q];
+        const float acc = pm_only ? F[a] : F[a] - c1 * s1 - c2 * s2;
+        const float vn = v[q] + kick * acc;
+        v[q] = vn;
+        if (!last) d[q] = dx[a] + (pm_only ? drift * vn : drift * vn + dD1 * s1 + dD2 * s2);
+    }
+}
+
+int launch_gather_kick_drift(const float2* f0, const float2* f1, const float2* f2, cola_state st, const double* row,
+                             int nq, int ng, double box, int last, int pm_only, int* status, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const int T = 256;
+    ProfScope ps(kKGatherKD, s);
+    k_gather_kick_drift<<<(unsigned)((np + T - 1) / T), T, 0, s>>>(
+        (const float*)f0, (const float*)f1, (const float*)f2, st.d, st.v, st.psi1, st.psi2, row, nq, ng,
+        2ll * fft_pitch(ng), (float)((double)ng / box), np, last, pm_only, status);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// fixed-point mesh -> delta (unpadded float ng^3); clears the fixed-point mesh
+// --------------------------------------------------------------------------
+__global__ void k_fix_to_delta(unsigned long long* dep, float* delta, long long n3, float scale) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    delta[i] = (float)dep[i] * scale - 1.0f;
+    dep[i] = 0ull;
+}
+
+int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s) {
+    const long long n3 = (long long)ng * ng * ng;
+    ProfScope ps(kKFixToDelta, s);
+    k_fix_to_delta<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(dep, delta, n3, scale);
+    return check_launch();
+}
+
+}  // namespace cola

@@ -1,0 +1,115 @@
+// Matter power spectrum shells (Sec. 2.4): P(k) = <|delta_k|^2> over the modes
+// of each k-bin, with optional CIC deconvolution and the Jing (2005) CIC
+// aliasing correction.
+//
+// Bin i (1 .. ng/2) holds the modes with (i - 1/2)^2 < |n|^2 < (i + 1/2)^2,
+// decided in integer arithmetic.  Half-spectrum modes count twice except on
+// the kz = 0 and kz = Nyquist planes.  P(k_n) = |delta_k|^2 L^3 / ng^6.
+// A fixed grid of blocks each accumulates its share of the modes into FP32
+// shared-memory bins; the per-block partials are then summed in FP64 in a
+// fixed block order.
+#include "cola_common.cuh"
+
+namespace cola {
+
+constexpr int kPkBlocks = 608;  // 4 blocks per SM on a 152-SM GB300
+constexpr int kPkThreads = 256;
+
+__global__ void k_pk_shells(const float2* __restrict__ mk, int ng, int P, float amp_scale, float kf, int flags,
+                            int nbins, double* __restrict__ part) {
+    extern __shared__ float bins[];  // 3 x nbins: sum w, sum w k, sum w P
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) bins[i] = 0.f;
+    __syncthreads();
+    const int H = ng / 2 + 1;
+    const long long total = (long long)ng * ng * H;
+    const int half = ng / 2;
+    const float inv_ng = 1.0f / (float)ng;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long row = e / H;
+        const int kz = (int)(e - row * H);
+        const int ix = (int)(row / ng), iy = (int)(row - (long long)ix * ng);
+        const int nx = ix < half ? ix : ix - ng;
+        const int ny = iy < half ? iy : iy - ng;
+        const long long n2 = (long long)nx * nx + (long long)ny * ny + (long long)kz * kz;
+        if (n2 == 0) continue;
+        int i = (int)(sqrtf((float)n2) + 0.5f);
+        while ((long long)i * i + i < n2) ++i;
+        while ((long long)i * i - i + 1 > n2) --i;
+        if (i < 1 || i > nbins) continue;
+        const float2 d = mk[row * P + kz];
+        const float dr = d.x * amp_scale, di = d.y * amp_scale;
+        float p = dr * dr + di * di;
+        if (flags & COLA_PK_DECONV_CIC) {
+            float W = 1.f;
+            const int nn[3] = {nx, ny, kz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (nn[a] != 0) {
+                    const float x = (float)nn[a] * inv_ng;
+                    const float sc = sinpif(x) / (3.14159265358979f * x);
+                    W *= sc * sc;
+                }
+            }
+            p /= W * W;
+        }
+        if (flags & COLA_PK_ALIAS_JING) {
+            float C = 1.f;
+            const int nn[3] = {nx, ny, kz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float s = sinpif((float)nn[a] * inv_ng);
+                C *= 1.f - 2.f / 3.f * s * s;
+            }
+            p /= C;
+        }
+        const float w = (kz == 0 || kz == half) ? 1.f : 2.f;
+        const float kmag = kf * sqrtf((float)n2);
+        atomicAdd(&bins[i - 1], w);
+        atomicAdd(&bins[nbins + i - 1], w * kmag);
+        atomicAdd(&bins[2 * nbins + i - 1], w * p);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x)
+        part[(size_t)blockIdx.x * 3 * nbins + i] = (double)bins[i];
+}
+
+__global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nbins, double* k, double* pk,
+                            double* nmodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbins) return;
+    double w = 0.0, wk = 0.0, wp = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double* q = part + (size_t)b * 3 * nbins;
+        w += q[i];
+        wk += q[nbins + i];
+        wp += q[2 * nbins + i];
+    }
+    nmodes[i] = w;
+    k[i] = w > 0.0 ? wk / w : 0.0;
+    pk[i] = w > 0.0 ? wp / w : 0.0;
+}
+
+int launch_power(const float2* mk, int ng, double box, int flags, double* part, double* k, double* pk,
+                 double* nmodes, int nbins, cudaStream_t s) {
+    const double ng3 = (double)ng * ng * ng;
+    const float amp_scale = (float)(box * sqrt(box) / ng3);  // sqrt(L^3 / ng^6)
+    const float kf = (float)(2.0 * 3.14159265358979323846 / box);
+    const size_t smem = (size_t)3 * nbins * sizeof(float);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_pk_shells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return COLA_ECUDA;
+    {
+        ProfScope ps(kKPkShells, s);
+        k_pk_shells<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, fft_pitch(ng), amp_scale, kf, flags, nbins, part);
+    }
+    int rc = check_launch();
+    if (rc) return rc;
+    ProfScope ps(kKPkReduce, s);
+    k_pk_reduce<<<(nbins + 127) / 128, 128, 0, s>>>(part, kPkBlocks, nbins, k, pk, nmodes);
+    return check_launch();
+}
+
+size_t power_partial_bytes(int nbins) { return (size_t)kPkBlocks * 3 * nbins * sizeof(double); }
+
+}  // namespace cola

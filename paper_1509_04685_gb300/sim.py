@@ -1,0 +1,68 @@
+"""Torch-allocated buffers around the C ABI: a Simulation owns the particle
+state (four SoA float32 tensors of shape (3, nq^3)) and the workspace, and
+forwards every call to the library.  No arithmetic of the method happens here."""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+
+class Simulation:
+    def __init__(self, cfg: L.cola_config, device="cuda", stream=None):
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.np = cfg.nq ** 3
+        self.ws_bytes = L.cola_workspace_size(cfg)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        f = lambda: torch.zeros((3, self.np), dtype=torch.float32, device=self.device)
+        self.d, self.v, self.psi1, self.psi2 = f(), f(), f(), f()
+        self.state = L.make_state(self.d, self.v, self.psi1, self.psi2)
+        self.stream = stream
+        self.node = 0
+
+    def init_tables(self):
+        L.cola_init(self.cfg, self.ws, self.stream)
+
+    def ic(self, seed: int):
+        L.cola_ic_2lpt(self.cfg, seed, self.state, self.ws, self.stream)
+        self.node = 0
+
+    def load_state(self, d, v, psi1, psi2):
+        for dst, src in ((self.d, d), (self.v, v), (self.psi1, psi1), (self.psi2, psi2)):
+            dst.copy_(torch.as_tensor(src).reshape(3, -1))
+
+    def step(self, j: int):
+        L.cola_step(self.cfg, self.state, j, self.ws, self.stream)
+        self.node = min(j + 1, self.cfg.n_steps - 1)
+
+    def run(self, steps=None):
+        for j in range(self.cfg.n_steps) if steps is None else steps:
+            self.step(j)
+
+    def force(self, a: float, out=None):
+        out = torch.empty((3, self.np), dtype=torch.float32, device=self.device) if out is None else out
+        L.cola_pm_force(self.cfg, self.state, a, out, self.ws, self.stream)
+        return out
+
+    def density(self):
+        ng = self.cfg.ng
+        out = torch.empty((ng, ng, ng), dtype=torch.float32, device=self.device)
+        L.cola_density(self.cfg, self.state, out, self.ws, self.stream)
+        return out
+
+    def power(self, ng_pk: int, a_out: float | None = None, flags: int = 0, node: int | None = None):
+        nb = ng_pk // 2
+        k, p, n = (torch.zeros(nb, dtype=torch.float64, device=self.device) for _ in range(3))
+        node = self.node if node is None else node
+        a = self.table()[node, 0].item() if a_out is None else a_out
+        L.cola_power_spectrum(self.cfg, self.state, node, a, ng_pk, flags, k, p, n, self.ws, self.stream)
+        return k, p, n
+
+    def table(self):
+        out = torch.empty((self.cfg.n_steps, 12), dtype=torch.float64, device=self.device)
+        L.cola_step_table(self.cfg, out, self.ws, self.stream)
+        return out
+
+    def status(self) -> int:
+        return L.cola_status(self.ws, self.stream)

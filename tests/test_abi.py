@@ -1,0 +1,59 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol that
+include/cola.h declares, and validates arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "cola.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|int32_t|uint64_t|const char\*)\s+(cola_\w+)\s*\(", text, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1509_04685_gb300 as C
+    names = _declared()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(C.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_workspace_size_and_validation():
+    import paper_1509_04685_gb300 as C
+    cfg = C.make_config(32, 96, 128.0, 0.05)
+    assert C.cola_workspace_size(cfg) > 96**3 * 8
+    for bad in (dict(nq=7), dict(ng=14), dict(ng=3), dict(ng=8192)):
+        kw = dict(nq=32, ng=96)
+        kw.update(bad)
+        with pytest.raises(C.ColaError) as e:
+            C.cola_workspace_size(C.make_config(kw["nq"], kw["ng"], 128.0, 0.05))
+        assert e.value.code in (-1, -3)
+    with pytest.raises(C.ColaError):
+        C.cola_workspace_size(C.make_config(32, 96, -1.0, 0.05))
+    with pytest.raises(C.ColaError):
+        C.cola_workspace_size(C.make_config(32, 96, 128.0, 0.05, n_steps=1))
+
+
+def test_entry_points_reject_bad_arguments_without_launching():
+    import paper_1509_04685_gb300 as C
+    L = C.LIB
+    cfg = C.make_config(8, 24, 32.0, 0.05)
+    size = C.cola_workspace_size(cfg)
+    fake = 1 << 40  # never dereferenced: every call below fails validation first
+    st = C.cola_state(fake, fake, fake, fake)
+    assert L.cola_step(ctypes.byref(cfg), ctypes.byref(st), 40, fake, size, None) == -1
+    assert L.cola_step(ctypes.byref(cfg), ctypes.byref(st), -1, fake, size, None) == -1
+    assert L.cola_step(ctypes.byref(cfg), ctypes.byref(st), 0, fake, size - 1, None) == -2
+    assert L.cola_step(ctypes.byref(cfg), ctypes.byref(st), 0, fake + 8, size, None) == -1
+    assert L.cola_pm_force(ctypes.byref(cfg), ctypes.byref(st), 0.5, None, fake, size, None) == -1
+    assert L.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), 0, 0.05, 48, 0, fake, fake, fake, 24,
+                                 fake, size, None) == -3  # ng_pk > ng
+    assert L.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), 0, 0.05, 24, 0, fake, fake, fake, 11,
+                                 fake, size, None) == -1  # nbins != ng_pk/2
+    assert C.cola_launch_count() == 0
+    assert C.cola_strerror(-6).startswith("non-finite")

@@ -1,0 +1,236 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (FP32 mesh/FFT/particle arithmetic against FP64):
+  single-step PM force rel-L2 <= 1e-5; 2LPT fields rel-L2 <= 1e-5;
+  FFT rel-L2 <= 1e-6; step table rel <= 1e-9 (both FP64);
+  P(k) per bin rel <= 1e-5 on identical positions, mode counts exact;
+  after a full 40-step run: P(k) within 1e-3 for k <= k_Ny/2 and rms
+  displacement difference <= 1e-3 of the mean inter-particle spacing.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cola as ocola
+from oracle import cosmology as cm
+from oracle import lpt, pm, power
+from synth import random_displacements, random_mesh
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1509_04685_gb300 as C  # noqa: E402
+
+from gpu_util import dev, f32, host, rel_l2  # noqa: E402
+
+COSMO = cm.Cosmology()
+
+
+def config(nq, ng, L, n_steps=40, a_init=0.05, **kw):
+    return C.make_config(nq, ng, L, a_init, 1.0, n_steps, **kw)
+
+
+@pytest.fixture(scope="module")
+def growth():
+    return cm.Growth(COSMO)
+
+
+@pytest.fixture(scope="module")
+def plin():
+    return cm.LinearPower(COSMO)
+
+
+# ---------------------------------------------------------------- FFT ------
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12, 18, 20, 30, 48, 96, 160, 250, 384])
+def test_fft3d_r2c_c2r_vs_numpy(n):
+    x = random_mesh(n, (n, n, n)).astype(np.float64)
+    P = C.cola_fft_pitch(n)
+    buf = torch.zeros((n, n, 2 * P), dtype=torch.float32, device="cuda")
+    buf[:, :, :n] = dev(x)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    C.cola_fft3d_r2c(n, buf, ws)
+    got = host(buf).reshape(n, n, P, 2)
+    got = got[..., 0] + 1j * got[..., 1]
+    ref = np.fft.rfftn(f32(x))
+    assert rel_l2(got[:, :, : n // 2 + 1], ref) < 1e-6
+    C.cola_fft3d_c2r(n, buf, ws)
+    back = host(buf)[:, :, :n] / n**3
+    assert rel_l2(back, f32(x)) < 1e-6
+
+
+def test_fft_rejects_bad_sizes():
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    buf = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    for n in (14, 7, 0, 8192):
+        with pytest.raises(C.ColaError):
+            C.cola_fft3d_r2c(n, buf, ws)
+
+
+# ---------------------------------------------------------------- tables ---
+@pytest.mark.parametrize("sampling,p", [(C.SAMPLING_LINEAR, 1.0), (C.SAMPLING_LOG, 1.0), (C.SAMPLING_POW, 0.8)])
+def test_step_table_vs_oracle(growth, sampling, p):
+    cfg = config(8, 16, 64.0, n_steps=12, a_init=1 / 40, sampling=sampling, sampling_p=p)
+    sim = C.Simulation(cfg)
+    sim.init_tables()
+    got = host(sim.table())
+    name = {C.SAMPLING_LINEAR: "linear", C.SAMPLING_LOG: "log", C.SAMPLING_POW: "pow"}[sampling]
+    a = cm.time_nodes(1 / 40, 1.0, 12, name, p)
+    t = cm.step_table(COSMO, a, growth)
+    for col, name in enumerate(C.TABLE_COLUMNS):
+        ref = getattr(t, name)
+        np.testing.assert_allclose(got[:, col], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max(), err_msg=name)
+
+
+# ---------------------------------------------------------------- deposit --
+@pytest.mark.parametrize("nq,ng,L", [(32, 96, 128.0), (6, 18, 30.0), (10, 30, 50.0), (8, 12, 40.0), (16, 16, 64.0)])
+def test_density_vs_oracle(nq, ng, L):
+    d = random_displacements(nq * 7 + ng, nq, 0.6 * L / nq)
+    cfg = config(nq, ng, L)
+    sim = C.Simulation(cfg)
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    got = host(sim.density())
+    ref = pm.density_contrast(f32(d), nq, ng, L)
+    m3 = (ng / nq) ** 3
+    assert np.abs(got - ref).max() < 3e-6 * m3 * (1 + np.abs(ref).max() / m3)
+    assert abs(got.mean()) < 1e-6 * m3
+    again = host(sim.density())
+    np.testing.assert_array_equal(got, again)  # fixed-point deposit is deterministic
+
+
+# ---------------------------------------------------------------- force ----
+def _oracle_state(seed, nq, L, plin, growth, a=0.05):
+    D1, _, D2, _ = growth(np.array([a]))
+    return lpt.initial_conditions(seed, nq, L, plin, D1[0], D2[0])
+
+
+@pytest.mark.parametrize("nq,ng,L", [(32, 96, 128.0), (16, 48, 64.0), (10, 30, 40.0), (12, 18, 48.0)])
+def test_pm_force_vs_oracle_initial_field(nq, ng, L, plin, growth):
+    st = _oracle_state(3, nq, L, plin, growth)
+    d = f32(st["d"])
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    got = host(sim.force(0.05))
+    ref = pm.pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / 0.05)
+    assert rel_l2(got, ref) < 1e-5
+
+
+def test_pm_force_vs_oracle_clustered(plin, growth):
+    # a strongly displaced state: 2LPT field scaled to a ~ 1 amplitude
+    nq, ng, L = 32, 96, 128.0
+    st = _oracle_state(5, nq, L, plin, growth, a=1.0)
+    d = f32(st["d"])
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    got = host(sim.force(1.0))
+    ref = pm.pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m)
+    assert rel_l2(got, ref) < 1e-5
+    assert np.abs(got.sum(axis=1)).max() < 1e-5 * np.abs(got).sum() / got.shape[1] * 10
+
+
+# ---------------------------------------------------------------- 2LPT -----
+@pytest.mark.parametrize("nq,L", [(32, 128.0), (18, 60.0), (20, 100.0)])
+def test_ic_2lpt_vs_oracle(nq, L, plin, growth):
+    sim = C.Simulation(config(nq, 3 * nq, L))
+    sim.ic(seed=42)
+    ref = _oracle_state(42, nq, L, plin, growth)
+    assert rel_l2(host(sim.psi1), ref["psi1"]) < 1e-5
+    assert rel_l2(host(sim.psi2), ref["psi2"]) < 1e-5
+    assert rel_l2(host(sim.d), ref["d"]) < 1e-5
+    assert np.all(host(sim.v) == 0)
+    assert sim.status() == 0
+
+
+# ---------------------------------------------------------------- step -----
+def test_single_cola_step_vs_oracle(plin, growth):
+    nq, ng, L = 32, 96, 128.0
+    tab = cm.step_table(COSMO, cm.time_nodes(0.05, 1.0, 40), growth)
+    ref = _oracle_state(9, nq, L, plin, growth)
+    rng = np.random.default_rng(0)
+    ref["v"] = rng.standard_normal(ref["d"].shape) * 0.05
+    for key in ref:
+        ref[key] = f32(ref[key])
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.load_state(*(dev(ref[k]) for k in ("d", "v", "psi1", "psi2")))
+    for j in (0, 17):
+        sim.load_state(*(dev(ref[k]) for k in ("d", "v", "psi1", "psi2")))
+        sim.step(j)
+        o = {k: v.copy() for k, v in ref.items()}
+        ocola.cola_step(o, j, tab, nq, ng, L)
+        dq = L / nq
+        assert np.sqrt(np.mean((host(sim.d) - o["d"]) ** 2)) < 1e-5 * dq
+        assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
+
+
+# ---------------------------------------------------------------- P(k) -----
+@pytest.mark.parametrize("flags", [0, C.PK_DECONV_CIC, C.PK_ALIAS_JING])
+def test_power_spectrum_vs_oracle(flags, plin, growth):
+    nq, ng, L = 32, 96, 128.0
+    st = _oracle_state(11, nq, L, plin, growth, a=0.5)
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.load_state(*(dev(f32(st[k])) for k in ("d", "v", "psi1", "psi2")))
+    for ng_pk in (64, 96):
+        k, p, n = (host(x) for x in sim.power(ng_pk, a_out=None, flags=flags, node=0))
+        kr, pr, nr = power.power_spectrum(f32(st["d"]), nq, ng_pk, L, flags)
+        np.testing.assert_array_equal(n, nr)
+        np.testing.assert_allclose(k, kr, rtol=1e-6)
+        np.testing.assert_allclose(p, pr, rtol=2e-5)
+
+
+def test_power_spectrum_snapshot_drift(plin, growth):
+    nq, ng, L = 16, 48, 64.0
+    st = _oracle_state(12, nq, L, plin, growth)
+    st["v"] = np.random.default_rng(1).standard_normal(st["d"].shape) * 0.1
+    for key in st:
+        st[key] = f32(st[key])
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.load_state(*(dev(st[k]) for k in ("d", "v", "psi1", "psi2")))
+    node = 5
+    a_node = cm.time_nodes(0.05, 1.0, 40)[node]
+    a_out = a_node + 0.01
+    k, p, n = (host(x) for x in sim.power(48, a_out=a_out, node=node))
+    dout = ocola.snapshot_displacement(st, a_node, a_out, growth, COSMO, cm.drift_integral)
+    kr, pr, nr = power.power_spectrum(dout, nq, 48, L)
+    np.testing.assert_allclose(p, pr, rtol=5e-5)
+
+
+# ---------------------------------------------------------------- run ------
+def test_full_run_small_config_vs_oracle(plin, growth):
+    """32^3 particles on a 96^3 mesh, L = 128 Mpc/h, 40 linear steps z = 19 -> 0."""
+    nq, ng, L = 32, 96, 128.0
+    cfg = config(nq, ng, L)
+    sim = C.Simulation(cfg)
+    sim.ic(seed=1)
+    sim.run()
+    assert sim.status() == 0
+    tab = cm.step_table(COSMO, cm.time_nodes(0.05, 1.0, 40), growth)
+    ref = _oracle_state(1, nq, L, plin, growth)
+    ocola.run(ref, tab, nq, ng, L)
+    dq = L / nq
+    rms = np.sqrt(np.mean(np.sum((host(sim.d) - ref["d"]) ** 2, axis=0)))
+    assert rms <= 1e-3 * dq
+    k, p, n = (host(x) for x in sim.power(ng, node=39))
+    kr, pr, nr = power.power_spectrum(ref["d"], nq, ng, L)
+    kny = np.pi * ng / L
+    sel = kr <= kny / 2
+    assert np.max(np.abs(p[sel] / pr[sel] - 1)) <= 1e-3
+
+
+def test_nonfinite_input_sets_status():
+    nq, ng, L = 8, 24, 32.0
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    d = np.zeros((3, nq**3), np.float32)
+    d[1, 17] = np.nan
+    sim.d.copy_(dev(d))
+    sim.density()
+    assert sim.status() == -6
+    assert sim.status() == 0  # cleared after reading
