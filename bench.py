@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "full": dict(name="cola_512^3_particles_1536^3_mesh_L1536_40steps", nq=512, ng=1536, box=1536.0),
+    "mid": dict(name="cola_256^3_particles_768^3_mesh_L768_40steps", nq=256, ng=768, box=768.0),
     "small": dict(name="cola_32^3_particles_96^3_mesh_L128_40steps", nq=32, ng=96, box=128.0),
 }
 A_INIT, N_NODES = 0.05, 40

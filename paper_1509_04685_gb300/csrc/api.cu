@@ -36,7 +36,11 @@ bool layout_for(const cola_config* cfg, Layout* L) {
     const size_t Mg = mesh_bytes(ng), Mq = mesh_bytes(nq);
     L->dep = align_up(kHdrBytes, 4096);
     L->mk = align_up(L->dep + (size_t)ng * ng * ng * 8, 4096);
-    for (int j = 0; j < 3; ++j) L->force[j] = align_up(L->mk + (j + 1) * Mg, 4096);
+    size_t end_prev = L->mk + Mg;
+    for (int j = 0; j < 3; ++j) {
+        L->force[j] = align_up(end_prev, 4096);
+        end_prev = L->force[j] + Mg;
+    }
     L->ic = L->dep;
     L->pk_part = L->force[0];
     size_t end = L->force[2] + Mg;

@@ -222,8 +222,8 @@ __device__ double tophat(double x) {
 
 // A = sigma8^2 / sigma_8,unnormalised^2 by composite Simpson in ln k over
 // [1e-7, 250] h/Mpc with 2^17 intervals; fixed-order block reduction.
-__global__ void k_sigma8(double* amp, CosmoD c) {
-    __shared__ double red[1024];
+__global__ void __launch_bounds__(256) k_sigma8(double* amp, CosmoD c) {
+    __shared__ double red[256];
     const int N = 1 << 17;
     const double lo = log(1e-7), hi = log(2e3 / 8.0);
     const double h = (hi - lo) / N;
@@ -384,7 +384,7 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
 
         ProfScope ps(kKIc, s);
 
-        k_sigma8<<<1, 1024, 0, s>>>(amp, c);
+        k_sigma8<<<1, 256, 0, s>>>(amp, c);
 
     }
     if ((rc = check_launch())) return rc;
