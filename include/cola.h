@@ -153,6 +153,21 @@ int cola_status(void* ws, size_t ws_bytes, void* stream);
  * side increments per launch). */
 uint64_t cola_launch_count(void);
 
+/* cola_density without any caller workspace, for callers that cannot hand the
+ * library scratch memory: e.g. a host application whose device memory is all
+ * owned by its own pool allocator, or an in-situ analysis inside a simulation
+ * that has reserved the whole device.  The paper has no counterpart; this is
+ * an integration convenience.  Same output as cola_density (delta as float[ng^3],
+ * deterministic).  The fixed-point deposit mesh lives in one file-scope device
+ * array of 128^3 cells (16 MiB per GPU that loads the library, held until the
+ * process exits): ng > 128 returns COLA_EUNSUPPORTED_SIZE.  Nothing is
+ * allocated.  The first call on each device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  Every call shares the array, so calls that overlap on the GPU
+ * (different streams or devices' contexts sharing it) race; each call clears
+ * it first.  Non-finite particle data turns the whole output into NaN. */
+int cola_density_noalloc(const cola_config* cfg, const cola_state* st, float* delta, void* stream);
+
 /* Per-kernel timing (tracing): between cola_profile_start and
  * cola_profile_stop every kernel launch of the library is bracketed by CUDA
  * events on its own stream (at most max_records launches are recorded).
