@@ -35,15 +35,10 @@ bool layout_for(const cola_config* cfg, Layout* L) {
     const int ng = cfg->ng, nq = cfg->nq;
     const size_t Mg = mesh_bytes(ng), Mq = mesh_bytes(nq);
     L->dep = align_up(kHdrBytes, 4096);
-    L->mk = align_up(L->dep + (size_t)ng * ng * ng * 8, 4096);
-    size_t end_prev = L->mk + Mg;
-    for (int j = 0; j < 3; ++j) {
-        L->force[j] = align_up(end_prev, 4096);
-        end_prev = L->force[j] + Mg;
-    }
+    L->F = align_up(L->dep + (size_t)ng * ng * ng * 8, 4096);
     L->ic = L->dep;
-    L->pk_part = L->force[0];
-    size_t end = L->force[2] + Mg;
+    L->pk_part = align_up(L->F + 2 * Mg, 4096);
+    size_t end = L->F + 3 * Mg;
     size_t ic_end = L->ic + 7 * Mq;
     size_t pk_end = L->pk_part + power_partial_bytes(ng / 2);
     if (ic_end > end) end = ic_end;
@@ -80,32 +75,29 @@ static double host_node_a(const cola_config* c, int j) {
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// deposit + forward z, y passes + fused x/Green pass + inverse y, z passes:
-// leaves the three force components in the real views of force[0..2].
+// deposit + forward z, y passes + fused x/Green pass + inverse y, z passes on
+// the interleaved force mesh F (rows (ix, iy, c) of P complex): delta_k lives
+// in component 0 until the x pass replaces it by F_x and adds F_y, F_z; the
+// inverse y and z passes then run over all three components in one launch each.
 static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
                           cudaStream_t s) {
     const int ng = cfg->ng, nq = cfg->nq;
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
-    float2* mk = reinterpret_cast<float2*>(wsp(ws, L.mk));
-    float2* f[3];
-    for (int j = 0; j < 3; ++j) f[j] = reinterpret_cast<float2*>(wsp(ws, L.force[j]));
+    float2* F = reinterpret_cast<float2*>(wsp(ws, L.F));
     const float2* tw = twiddle_ptr(ws, kTwMesh);
     const double ratio = (double)ng / (double)nq;
     const float scale = (float)(ratio * ratio * ratio / 1099511627776.0);
     const double ng3 = (double)ng * ng * ng;
+    const long long P = fft_pitch(ng), n2 = (long long)ng * ng;
     int rc;
     if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws), s)))
         return rc;
-    if ((rc = fft_z_r2c(dep, mk, ng, scale, tw, s))) return rc;
-    if ((rc = fft_strided(mk, ng, 1, -1, tw, s))) return rc;
-    if ((rc = fft_x_green(mk, f[0], f[1], f[2], ng, (float)(green / ng3),
-                          (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s)))
+    if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, 3 * P, n2))) return rc;
+    if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * P, ng, 1, ng * 3 * P, 0}, kKYFwd))) return rc;
+    if ((rc = fft_x_green(F, ng, (float)(green / ng3), (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s)))
         return rc;
-    for (int j = 0; j < 3; ++j) {
-        if ((rc = fft_strided(f[j], ng, 1, +1, tw, s))) return rc;
-        if ((rc = fft_z_c2r(f[j], ng, tw, s, nullptr, 0, 1.f))) return rc;
-    }
-    return COLA_OK;
+    if ((rc = fft_lines(F, ng, +1, tw, s, LineGeom{3 * P, 3 * ng, 3, ng * 3 * P, P}, kKYInv))) return rc;
+    return fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2);
 }
 
 static const float2* twiddles_for(int n, const cola_config* cfg, void* ws, cudaStream_t s, int* rc) {
@@ -168,9 +160,7 @@ int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float*
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / a;
     if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
-    return launch_gather(reinterpret_cast<float2*>(wsp(ws, L.force[0])),
-                         reinterpret_cast<float2*>(wsp(ws, L.force[1])),
-                         reinterpret_cast<float2*>(wsp(ws, L.force[2])), st->d, force, cfg->nq, cfg->ng, cfg->box, s);
+    return launch_gather(reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, force, cfg->nq, cfg->ng, cfg->box, s);
 }
 
 int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, void* stream) {
@@ -181,9 +171,7 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
     if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
-    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.force[0])),
-                                    reinterpret_cast<float2*>(wsp(ws, L.force[1])),
-                                    reinterpret_cast<float2*>(wsp(ws, L.force[2])), *st,
+    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st,
                                     table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
                                     step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
                                     status_ptr(ws), s);
@@ -208,17 +196,20 @@ int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t no
         snap = sp;
     }
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
-    float2* mk = reinterpret_cast<float2*>(wsp(ws, L.mk));
+    float2* mk = reinterpret_cast<float2*>(wsp(ws, L.F));  // plain ng_pk mesh in the force-mesh region
     const float2* tw = twiddles_for(ng_pk, cfg, ws, s, &rc);
     if (rc) return rc;
     const double ratio = (double)ng_pk / (double)cfg->nq;
     if ((rc = launch_deposit_ex(st->d, st->v, st->psi1, st->psi2, dep, cfg->nq, ng_pk, cfg->box, snap,
                                 status_ptr(ws), s)))
         return rc;
-    if ((rc = fft_z_r2c(dep, mk, ng_pk, (float)(ratio * ratio * ratio / 1099511627776.0), tw, s))) return rc;
+    const long long Ppk = fft_pitch(ng_pk);
+    if ((rc = fft_z_r2c(dep, mk, ng_pk, (float)(ratio * ratio * ratio / 1099511627776.0), tw, s, Ppk,
+                        (long long)ng_pk * ng_pk)))
+        return rc;
     if ((rc = fft_strided(mk, ng_pk, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(mk, ng_pk, 0, -1, tw, s))) return rc;
-    return launch_power(mk, ng_pk, cfg->box, flags, reinterpret_cast<double*>(wsp(ws, L.pk_part)), k, pk, nmodes,
+    return launch_power(mk, ng_pk, Ppk, cfg->box, flags, reinterpret_cast<double*>(wsp(ws, L.pk_part)), k, pk, nmodes,
                         nbins, s);
 }
 
@@ -265,7 +256,7 @@ int cola_fft3d_r2c(int32_t n, float* data, void* ws, size_t ws_bytes, void* stre
     const float2* tw = twiddles_for(n, nullptr, ws, s, &rc);
     if (rc) return rc;
     float2* c = reinterpret_cast<float2*>(data);
-    if ((rc = fft_z_r2c(nullptr, c, n, 0.f, tw, s))) return rc;
+    if ((rc = fft_z_r2c(nullptr, c, n, 0.f, tw, s, fft_pitch(n), (long long)n * n))) return rc;
     if ((rc = fft_strided(c, n, 1, -1, tw, s))) return rc;
     return fft_strided(c, n, 0, -1, tw, s);
 }
@@ -279,7 +270,7 @@ int cola_fft3d_c2r(int32_t n, float* data, void* ws, size_t ws_bytes, void* stre
     float2* c = reinterpret_cast<float2*>(data);
     if ((rc = fft_strided(c, n, 0, +1, tw, s))) return rc;
     if ((rc = fft_strided(c, n, 1, +1, tw, s))) return rc;
-    return fft_z_c2r(c, n, tw, s, nullptr, 0, 1.f);
+    return fft_z_c2r(c, n, tw, s, nullptr, 0, 1.f, fft_pitch(n), (long long)n * n);
 }
 
 int cola_status(void* ws, size_t ws_bytes, void* stream) {

@@ -111,85 +111,275 @@ struct SmallDft<8> {
     }
 };
 
+template <>
+struct SmallDft<16> {
+    // 4 x 4: DFT4 over stride-4 groups, twiddle by W16^(a b), DFT4 again
+    __device__ __forceinline__ static void run(float2* v, int sign) {
+        const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, r = 0.70710678118654752440f;
+        float2 g[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[a][q] = v[a + 4 * q];
+            SmallDft<4>::run(g[a], sign);  // g[a][b] = sum_q v[a+4q] W4^(qb)
+        }
+        // twiddle W16^(a b) = exp(sign 2 pi i a b / 16)
+        const float2 w1 = make_float2(c1, sign * s1), w2 = make_float2(r, sign * r), w3 = make_float2(s1, sign * c1);
+        const float2 w6 = make_float2(-r, sign * r), w9 = make_float2(-c1, -sign * s1);
+        g[1][1] = cmul(g[1][1], w1);
+        g[1][2] = cmul(g[1][2], w2);
+        g[1][3] = cmul(g[1][3], w3);
+        g[2][1] = cmul(g[2][1], w2);
+        g[2][2] = cmul_isign(g[2][2], sign);
+        g[2][3] = cmul(g[2][3], w6);
+        g[3][1] = cmul(g[3][1], w3);
+        g[3][2] = cmul(g[3][2], w6);
+        g[3][3] = cmul(g[3][3], w9);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float2 t[4] = {g[0][b], g[1][b], g[2][b], g[3][b]};
+            SmallDft<4>::run(t, sign);  // X[b + 4c] = sum_a t[a] W4^(ac)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[b + 4 * c] = t[c];
+        }
+    }
+};
+
+// Radix P*Q (coprime P, Q, Good-Thomas index map): 6 = 2 x 3, 12 = 4 x 3.
+template <int P, int Q>
+__device__ __forceinline__ void pfa_dft(float2* v, int sign) {
+    constexpr int N = P * Q;
+    float2 g[Q][P];
+    // input n = (P a + Q b) mod N -> g[a'][b] with a' indexing Q, b indexing P
+#pragma unroll
+    for (int a = 0; a < Q; ++a)
+#pragma unroll
+        for (int b = 0; b < P; ++b) g[a][b] = v[(P * a + Q * b) % N];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) SmallDft<P>::run(g[a], sign);
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        float2 t[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) t[a] = g[a][b];
+        SmallDft<Q>::run(t, sign);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) g[a][b] = t[a];
+    }
+    // output k with k = c1 (mod P), k = c2 (mod Q): CRT
+#pragma unroll
+    for (int c2 = 0; c2 < Q; ++c2)
+#pragma unroll
+        for (int c1 = 0; c1 < P; ++c1) {
+            int k = 0;
+#pragma unroll
+            for (int t = 0; t < N; ++t)
+                if (t % P == c1 && t % Q == c2) k = t;
+            v[k] = g[c2][c1];
+        }
+}
+
+template <>
+struct SmallDft<6> {
+    __device__ __forceinline__ static void run(float2* v, int sign) { pfa_dft<2, 3>(v, sign); }
+};
+template <>
+struct SmallDft<12> {
+    __device__ __forceinline__ static void run(float2* v, int sign) { pfa_dft<4, 3>(v, sign); }
+};
+
 // ---------------------------------------------------------------------------
 // FFT plan: n = product of radices (applied in order), n <= kMaxFft
 // ---------------------------------------------------------------------------
 constexpr int kMaxFft = 4096;   // largest line length
 constexpr int kMaxRadices = 16;
 
+// Exact division by a runtime constant d for numerators n with n * d < 2^32:
+// q = umulhi(n, ceil(2^32 / d)) (d = 1 handled apart).
+struct FastDiv {
+    unsigned d, m;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+    return FastDiv{d, d <= 1 ? 0u : (unsigned)(((1ull << 32) + d - 1) / d)};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) { return f.d <= 1 ? n : __umulhi(n, f.m); }
+
 struct FftPlan {
     int n;
     int nr;
     int radix[kMaxRadices];
+    FastDiv ls_div[kMaxRadices];   // division by Ls (product of the radices before pass s)
+    FastDiv nbl_div[kMaxRadices];  // division by n / radix[s]
 };
 
 // Factor n into radices 8, 4, 2, 3, 5 (largest powers of two first).
 // Returns false if n has another prime factor or is out of range.
 bool make_plan(int n, FftPlan* p);
 
-// One Stockham autosort pass (Govindaraju et al. 2008 "expand" form) over nl
-// lines of length n held in shared memory, from src to dst: element i of line
-// l at buf[l*ls + i*es].  Ls = product of the radices already applied;
-// tw[q * twmul] = exp(-2 pi i q / n) for q < n.
-//   butterfly j (0 <= j < n/R), k = j mod Ls:
-//   v_r = src[j + r n/R] * W_{Ls R}^{r k},  v = DFT_R(v),
-//   dst[(j / Ls) Ls R + k + r Ls] = v_r.
-template <int R>
-__device__ __forceinline__ void stockham_pass(const float2* __restrict__ src, float2* __restrict__ dst, int n, int nl,
-                                              int ls, int es, bool line_fast, int Ls, const float2* __restrict__ tw,
-                                              int twmul, int sign) {
+// ---------------------------------------------------------------------------
+// Stockham autosort passes (Govindaraju et al. 2008, "expand" form) over nl
+// lines of length n, reading through an input accessor and writing through an
+// output accessor.  Butterfly j of line l (0 <= j < n/R), k = j mod Ls:
+//   v_r = in(l, j + r n/R) * W_{Ls R}^{r k},  v = DFT_R(v),
+//   out(l, (j / Ls) Ls R + k + r Ls) = v_r
+// with Ls the product of the radices already applied and
+// tw[q * twmul] = exp(-2 pi i q / n).  Accessors give load<R>(l, i0, di, v)
+// (v_r = x(l, i0 + r di)) and store<R>(l, i0, di, v).
+// The first pass of a transform reads global memory directly and the last
+// one may write it directly, so a transform of p passes moves its data
+// through shared memory only p - 1 times.
+// ---------------------------------------------------------------------------
+// Shared-memory element i of a line sits at i + i/16: one pad slot per 16
+// elements keeps the stride-R accesses of a Stockham pass off a single bank.
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+
+struct SmemIO {
+    float2* p;
+    int ls, es;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[l * ls + spad(i0 + r * di) * es];
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[l * ls + spad(i0 + r * di) * es] = v[r];
+    }
+};
+
+template <int R, int SIGN, bool LF, class In, class Out>
+__device__ __forceinline__ void fft_pass(const In& in, const Out& out, int n, int nl, int nl_shift, int Ls,
+                                         FastDiv lsd, FastDiv nbld, const float2* __restrict__ tw, int twmul) {
+    constexpr int sign = SIGN;
+    constexpr bool line_fast = LF;
     const int nbl = n / R;
     const int nb = nbl * nl;
     const int twstep = (n / (Ls * R)) * twmul;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         int l, j;
         if (line_fast) {
-            l = b % nl;
-            j = b / nl;
+            l = b & (nl - 1);
+            j = b >> nl_shift;
         } else {
-            j = b % nbl;
-            l = b / nbl;
+            l = (int)fdiv((unsigned)b, nbld);
+            j = b - l * nbl;
         }
-        const int k = j % Ls;
-        const float2* s = src + l * ls;
+        const int jq = (int)fdiv((unsigned)j, lsd);
+        const int k = j - jq * Ls;
         float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[(j + r * nbl) * es];
+        in.template load<R>(l, j, nbl, v);
         if (Ls > 1) {
+            const int step = k * twstep;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tw[r * k * twstep]);
+                float2 w = tw[r * step];
                 if (sign > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
         }
         SmallDft<R>::run(v, sign);
-        float2* d = dst + l * ls + ((j / Ls) * Ls * R + k) * es;
-#pragma unroll
-        for (int r = 0; r < R; ++r) d[r * Ls * es] = v[r];
+        out.template store<R>(l, jq * Ls * R + k, Ls, v);
     }
-    __syncthreads();
 }
 
-// Full FFT of nl lines in shared memory, ping-ponging between a and b (the
-// caller has synchronised after filling a).  Returns the buffer holding the
-// result; returns synchronised.
-__device__ __forceinline__ float2* fft_smem(float2* a, float2* b, const FftPlan& plan, int nl, int ls, int es,
-                                            bool line_fast, const float2* __restrict__ tw, int twmul, int sign) {
+template <int SIGN, bool LF, class In, class Out>
+__device__ __forceinline__ void fft_pass_any(int R, const In& in, const Out& out, int n, int nl, int nl_shift, int Ls,
+                                             FastDiv lsd, FastDiv nbld, const float2* __restrict__ tw, int twmul) {
+    switch (R) {
+        case 16: fft_pass<16, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 12: fft_pass<12, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 8: fft_pass<8, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 6: fft_pass<6, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 5: fft_pass<5, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 4: fft_pass<4, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        case 3: fft_pass<3, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+        default: fft_pass<2, SIGN, LF>(in, out, n, nl, nl_shift, Ls, lsd, nbld, tw, twmul); break;
+    }
+}
+
+struct LineGeom {
+    long long S;   // element stride along the transformed axis
+    int nouter;    // number of outer indices
+    int o2n;       // outer index o = o1 * o2n + o2
+    long long s1, s2;
+};
+
+struct FftGeom {
+    int nl;          // lines per block
+    int ls, es;      // shared-memory layout: element i of line l at l*ls + i*es
+    bool line_fast;  // butterfly index runs over lines first (needs nl = 2^nl_shift)
+    int nl_shift;
+    int twmul;       // table stride: tw is the table of n*twmul
+};
+
+// Transform reading `in`, all intermediate passes in shared memory (ping-pong
+// a/b), last pass written through `out`.  Returns synchronised.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// `hook` runs (uniformly, by every thread) right after the first pass, when
+// the input accessor's memory is no longer needed.
+template <int SIGN, bool LF, class In, class Out, class Hook = NoHook>
+__device__ __forceinline__ void fft_run_out(const In& in, const Out& out, float2* a, float2* b, const FftPlan& plan,
+                                            const FftGeom& g, const float2* __restrict__ tw,
+                                            const Hook& hook = Hook()) {
     int Ls = 1;
-    for (int s = 0; s < plan.nr; ++s) {
-        const int R = plan.radix[s];
-        switch (R) {
-            case 8: stockham_pass<8>(a, b, plan.n, nl, ls, es, line_fast, Ls, tw, twmul, sign); break;
-            case 4: stockham_pass<4>(a, b, plan.n, nl, ls, es, line_fast, Ls, tw, twmul, sign); break;
-            case 2: stockham_pass<2>(a, b, plan.n, nl, ls, es, line_fast, Ls, tw, twmul, sign); break;
-            case 3: stockham_pass<3>(a, b, plan.n, nl, ls, es, line_fast, Ls, tw, twmul, sign); break;
-            default: stockham_pass<5>(a, b, plan.n, nl, ls, es, line_fast, Ls, tw, twmul, sign); break;
+    if (plan.nr == 1) {
+        // single pass: go through shared memory so that in-place callers never
+        // store an element another thread has still to load
+        fft_pass_any<SIGN, LF>(plan.radix[0], in, SmemIO{a, g.ls, g.es}, plan.n, g.nl, g.nl_shift, 1, plan.ls_div[0],
+                           plan.nbl_div[0], tw, g.twmul);
+        __syncthreads();
+        hook();
+        for (int e = threadIdx.x; e < plan.n * g.nl; e += blockDim.x) {
+            const int l = LF ? (e & (g.nl - 1)) : e / plan.n;
+            const int i = LF ? (e >> g.nl_shift) : e - l * plan.n;
+            const float2 v = a[l * g.ls + spad(i) * g.es];
+            out.template store<1>(l, i, 1, &v);
         }
+        __syncthreads();
+        return;
+    }
+    fft_pass_any<SIGN, LF>(plan.radix[0], in, SmemIO{a, g.ls, g.es}, plan.n, g.nl, g.nl_shift, 1, plan.ls_div[0],
+                           plan.nbl_div[0], tw, g.twmul);
+    __syncthreads();
+    hook();
+    Ls = plan.radix[0];
+    for (int s = 1; s + 1 < plan.nr; ++s) {
+        fft_pass_any<SIGN, LF>(plan.radix[s], SmemIO{a, g.ls, g.es}, SmemIO{b, g.ls, g.es}, plan.n, g.nl,
+                               g.nl_shift, Ls, plan.ls_div[s], plan.nbl_div[s], tw, g.twmul);
+        __syncthreads();
         float2* t = a;
         a = b;
         b = t;
-        Ls *= R;
+        Ls *= plan.radix[s];
+    }
+    const int s = plan.nr - 1;
+    fft_pass_any<SIGN, LF>(plan.radix[s], SmemIO{a, g.ls, g.es}, out, plan.n, g.nl, g.nl_shift, Ls, plan.ls_div[s],
+                           plan.nbl_div[s], tw, g.twmul);
+    __syncthreads();
+}
+
+// Same, with the result left in shared memory; returns the buffer holding it.
+template <int SIGN, bool LF, class In, class Hook = NoHook>
+__device__ __forceinline__ float2* fft_run_smem(const In& in, float2* a, float2* b, const FftPlan& plan,
+                                                const FftGeom& g, const float2* __restrict__ tw,
+                                                const Hook& hook = Hook()) {
+    fft_pass_any<SIGN, LF>(plan.radix[0], in, SmemIO{a, g.ls, g.es}, plan.n, g.nl, g.nl_shift, 1, plan.ls_div[0],
+                           plan.nbl_div[0], tw, g.twmul);
+    __syncthreads();
+    hook();
+    int Ls = plan.radix[0];
+    for (int s = 1; s < plan.nr; ++s) {
+        fft_pass_any<SIGN, LF>(plan.radix[s], SmemIO{a, g.ls, g.es}, SmemIO{b, g.ls, g.es}, plan.n, g.nl,
+                               g.nl_shift, Ls, plan.ls_div[s], plan.nbl_div[s], tw, g.twmul);
+        __syncthreads();
+        float2* t = a;
+        a = b;
+        b = t;
+        Ls *= plan.radix[s];
     }
     return a;
 }
@@ -211,10 +401,9 @@ enum TwSlot { kTwMesh = 0, kTwLagr = 1, kTwScratch = 2 };
 
 struct Layout {
     size_t dep;        // uint64 fixed-point CIC mesh, ng^3 (zero between calls)
-    size_t mk;         // complex mesh ng x ng x P
-    size_t force[3];   // three complex/real meshes ng x ng x P
+    size_t F;          // interleaved force mesh: ng x ng x 3 rows of P complex (delta_k in component 0)
     size_t ic;         // 2LPT scratch: 7 complex meshes of nq x nq x Pq (aliases dep..)
-    size_t pk_part;    // P(k) per-block partial sums (aliases force[0])
+    size_t pk_part;    // P(k) per-block partial sums (after the first two thirds of F)
     size_t total;
 };
 
@@ -231,6 +420,28 @@ inline int* status_ptr(void* ws) { return reinterpret_cast<int*>(wsp(ws, kHdrSta
 inline double* table_ptr(void* ws) { return reinterpret_cast<double*>(wsp(ws, kHdrTable)); }
 inline float2* twiddle_ptr(void* ws, int slot) {
     return reinterpret_cast<float2*>(wsp(ws, kHdrTwiddle + (size_t)slot * kMaxFft * 8));
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (16 bytes, L2 only) for tile prefetch
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Stage an n x B tile (rows i at stride S, B adjacent complex columns) into
+// shared memory with the padded line layout (l + spad(i) B), 16 bytes at a time.
+__device__ __forceinline__ void tile_prefetch(float2* stg, const float2* g, int n, int B, long long S) {
+    const int hb = B >> 1;
+    const int hs = __ffs(hb) - 1;
+    for (int e = threadIdx.x; e < n * hb; e += blockDim.x) {
+        const int i = e >> hs, c = (e & (hb - 1)) << 1;
+        cp_async16(stg + c + spad(i) * B, g + (long long)i * S + c);
+    }
+    cp_async_commit();
 }
 
 // device status latch
@@ -262,24 +473,30 @@ inline int check_launch() {
 }
 
 int launch_twiddles(float2* tw, int n, cudaStream_t s);
-int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s);
-int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale);
+// z passes: row r at base + r*rs (complex units), nrows rows
+int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,
+              long long rs, long long nrows);
+int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale,
+              long long rs, long long nrows);
+// line passes: tile of outer index o starts at (o / o2n) s1 + (o % o2n) s2, element stride S
+int fft_lines(float2* data, int n, int sign, const float2* tw, cudaStream_t s, LineGeom lg, int kid);
+// plain n x n x P mesh, axis 1 = y, 0 = x
 int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaStream_t s);
-int fft_x_green(const float2* mk, float2* f0, float2* f1, float2* f2, int n, float gscale, float kf,
-                const float2* tw, cudaStream_t s);
+// interleaved force mesh (rows (ix, iy, c)): delta_k in c = 0 -> F_x, F_y, F_z in c = 0, 1, 2
+int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s);
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
                       int nq, int ng, double box, const double* snap, int* status, cudaStream_t s);
-int launch_gather(const float2* f0, const float2* f1, const float2* f2, const float* d, float* out, int nq, int ng,
-                  double box, cudaStream_t s);
-int launch_gather_kick_drift(const float2* f0, const float2* f1, const float2* f2, cola_state st, const double* row,
-                             int nq, int ng, double box, int last, int pm_only, int* status, cudaStream_t s);
+// F: interleaved force mesh, real view, component c of (ix, iy) at ((ix n + iy) 3 + c) 2P floats
+int launch_gather(const float2* F, const float* d, float* out, int nq, int ng, double box, cudaStream_t s);
+int launch_gather_kick_drift(const float2* F, cola_state st, const double* row, int nq, int ng, double box, int last,
+                             int pm_only, int* status, cudaStream_t s);
 int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s);
 
 int launch_tables(const cola_config* cfg, double* table, cudaStream_t s);
 int launch_snapshot_coeffs(const cola_config* cfg, double a_node, double a_out, double* snap, cudaStream_t s);
 int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, const Layout& L, cudaStream_t s);
-int launch_power(const float2* mk, int ng, double box, int flags, double* part, double* k, double* pk,
+int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
                  double* nmodes, int nbins, cudaStream_t s);
 size_t power_partial_bytes(int nbins);
 

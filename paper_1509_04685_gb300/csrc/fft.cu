@@ -14,31 +14,44 @@ namespace cola {
 
 unsigned long long g_launches = 0;
 
+// Radices 16, 12, 8, 6, 5, 4, 3, 2: threes are paired with spare factors of
+// two (12 = 4*3, 6 = 2*3), the remaining twos go in 16s, then 8/4/2.
 bool make_plan(int n, FftPlan* p) {
     if (n < 1 || n > kMaxFft) return false;
+    int m = n, a = 0, b = 0, c = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    while (m % 5 == 0) { m /= 5; ++c; }
+    if (m != 1) return false;
+    int list[kMaxRadices], nr = 0;
+    auto push = [&](int r) { if (nr < kMaxRadices) list[nr++] = r; };
+    int pairs = b < a / 2 ? b : a / 2;
+    for (int i = 0; i < pairs; ++i) push(12);
+    a -= 2 * pairs;
+    b -= pairs;
+    if (b > 0 && a > 0) { push(6); --a; --b; }
+    while (a >= 4) { push(16); a -= 4; }
+    if (a == 3) push(8);
+    if (a == 2) push(4);
+    if (a == 1) push(2);
+    while (b-- > 0) push(3);
+    while (c-- > 0) push(5);
+    // largest radix first (the first pass reads global memory and needs no twiddles)
+    for (int i = 0; i < nr; ++i)
+        for (int j = i + 1; j < nr; ++j)
+            if (list[j] > list[i]) { int t = list[i]; list[i] = list[j]; list[j] = t; }
     p->n = n;
-    p->nr = 0;
-    int m = n;
-    const int order[5] = {8, 4, 2, 3, 5};
-    for (int r : order) {
-        while (m % r == 0) {
-            if (p->nr >= kMaxRadices) return false;
-            p->radix[p->nr++] = r;
-            m /= r;
-        }
+    p->nr = nr;
+    int Ls = 1;
+    for (int s = 0; s < nr; ++s) {
+        p->radix[s] = list[s];
+        p->ls_div[s] = make_fastdiv(Ls);
+        p->nbl_div[s] = make_fastdiv(n / list[s]);
+        Ls *= list[s];
     }
-    return m == 1;
+    return true;
 }
 
-// about twelve complex elements per thread, 64 .. 512 threads (two blocks of
-// ~48-register threads fit on an SM)
-static int round_threads(long elems) {
-    long t = (elems + 11) / 12;
-    t = (t + 31) / 32 * 32;
-    if (t < 64) t = 64;
-    if (t > 512) t = 512;
-    return (int)t;
-}
 
 // ---------------------------------------------------------------------------
 // twiddles: tw[q] = exp(-2 pi i q / n), FP64 sincospi rounded once to FP32
@@ -58,6 +71,160 @@ int launch_twiddles(float2* tw, int n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// accessors for the z (row) passes.  Line l of a block is mesh row row0 + l.
+// ---------------------------------------------------------------------------
+// fixed-point CIC counts (2^40 per particle) -> delta = count*scale - 1, packed
+// as complex pairs; every count is cleared after it is read.
+struct FixRowLoader {
+    unsigned long long* dep;
+    int n;
+    long long row0, nrows;
+    float scale;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+        const long long row = row0 + l;
+        if (row >= nrows) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+            return;
+        }
+        ulonglong2* p = reinterpret_cast<ulonglong2*>(dep + row * n);
+        ulonglong2 c[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) c[r] = __ldcs(p + i0 + r * di);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = make_float2((float)c[r].x * scale - 1.0f, (float)c[r].y * scale - 1.0f);
+            __stcs(p + i0 + r * di, make_ulonglong2(0ull, 0ull));
+        }
+    }
+};
+
+// real rows (row pitch P complex) packed as complex pairs
+struct RowLoader {
+    const float2* data;
+    long long rs;  // row stride (complex)
+    long long row0, nrows;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+        const long long row = row0 + l;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = row < nrows ? data[row * rs + i0 + r * di] : make_float2(0.f, 0.f);
+    }
+};
+
+// c2r pre-processing: Z[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) W_n^-k,
+// with Im X[0] and Im X[M] ignored.
+struct C2rLoader {
+    const float2* data;
+    long long rs;
+    int M;
+    long long row0, nrows;
+    const float2* tw;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+        const long long row = row0 + l;
+        if (row >= nrows) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+            return;
+        }
+        const float2* x = data + row * rs;
+        float2 a[R], bb[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = i0 + r * di;
+            a[r] = x[k];
+            bb[r] = x[M - k];
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = i0 + r * di;
+            if (k == 0) {
+                a[r].y = 0.f;
+                bb[r].y = 0.f;
+            }
+            const float2 b = cconj(bb[r]);
+            float2 w = __ldg(tw + k);
+            w.y = -w.y;
+            const float2 d = cmul(csub(a[r], b), w);
+            v[r] = make_float2(a[r].x + b.x - d.y, a[r].y + b.y + d.x);
+        }
+    }
+};
+
+// z[m] written as the float pair (2m, 2m+1) of real row row0 + l
+struct RowStore {
+    float2* data;
+    long long rs;
+    long long row0, nrows;
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+        const long long row = row0 + l;
+        if (row >= nrows) return;
+#pragma unroll
+        for (int r = 0; r < R; ++r) data[row * rs + i0 + r * di] = v[r];
+    }
+};
+
+// same, scaled, into a plain float array with row pitch opitch
+struct RowStoreGeneric {
+    float* out;
+    long long opitch;
+    float scale;
+    long long row0, nrows;
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+        const long long row = row0 + l;
+        if (row >= nrows) return;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long q = row * opitch + 2 * (i0 + r * di);
+            out[q] = v[r].x * scale;
+            out[q + 1] = v[r].y * scale;
+        }
+    }
+};
+
+// strided tile (y or x pass): line l = column col0 + l, element i at row stride S
+struct ColIO {
+    float2* g;
+    long long S;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcs(g + (long long)(i0 + r * di) * S + l);
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(g + (long long)(i0 + r * di) * S + l, v[r]);
+    }
+};
+
+// Psi = IFFT_x(phi) stored twice: F_y = i k_y Psi and F_z = i k_z Psi.  Along
+// an x line k_y (fixed row iy) and k_z (fixed column) are constants, so they
+// commute with the inverse x transform: one transform serves both components.
+struct YZStore {
+    float2* fy;
+    float2* fz;
+    long long S;
+    float ky;             // 0 on the y Nyquist plane
+    float kf;
+    int col0, half;
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+        const float kz = (col0 + l == half) ? 0.f : kf * (float)(col0 + l);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long q = (long long)(i0 + r * di) * S + l;
+            __stcs(fy + q, make_float2(-ky * v[r].y, ky * v[r].x));
+            __stcs(fz + q, make_float2(-kz * v[r].y, kz * v[r].x));
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // z pass, forward r2c.  FIX: input is the uint64 fixed-point CIC mesh (rows of
 // n counts, 2^40 per particle), converted to delta = count*scale - 1 and
 // cleared after reading; otherwise the input is the real view of `out`.
@@ -65,201 +232,173 @@ int launch_twiddles(float2* tw, int n, cudaStream_t s) {
 // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[M-k])/2, O = (Z[k] - conj Z[M-k])/(2i).
 // ---------------------------------------------------------------------------
 template <bool FIX>
-__global__ void k_fft_z_r2c(unsigned long long* __restrict__ dep, float2* out, int n, int P, long long nrows,
-                            int NR, float scale, FftPlan plan, const float2* __restrict__ tw) {
+__global__ void k_fft_z_r2c(unsigned long long* __restrict__ dep, float2* out, int n, long long rs, long long nrows,
+                            int NR, float scale, FftPlan plan, const float2* __restrict__ tw, FastDiv m1div) {
     extern __shared__ float2 sm[];
     const int M = n / 2;
-    const int ls = M + 1;
+    const int ls = spad(M) + 1;
     float2* sb = sm + NR * ls;
     const long long row0 = (long long)blockIdx.x * NR;
-    const int T = blockDim.x;
-    for (int e = threadIdx.x; e < NR * M; e += T) {
-        const int l = e / M, m = e - l * M;
-        const long long row = row0 + l;
-        float2 v = make_float2(0.f, 0.f);
-        if (row < nrows) {
-            if (FIX) {
-                ulonglong2* p = reinterpret_cast<ulonglong2*>(dep + row * n) + m;
-                ulonglong2 c = *p;
-                v = make_float2((float)c.x * scale - 1.0f, (float)c.y * scale - 1.0f);
-                *p = make_ulonglong2(0ull, 0ull);
-            } else {
-                v = out[row * P + m];
-            }
-        }
-        sm[l * ls + m] = v;
-    }
-    __syncthreads();
-    const float2* Z = fft_smem(sm, sb, plan, NR, ls, 1, false, tw, 2, -1);
-    for (int e = threadIdx.x; e < NR * (M + 1); e += T) {
-        const int l = e / (M + 1), k = e - l * (M + 1);
+    const FftGeom g{NR, ls, 1, false, 0, 2};
+    const float2* Z;
+    if (FIX)
+        Z = fft_run_smem<-1, false>(FixRowLoader{dep, n, row0, nrows, scale}, sm, sb, plan, g, tw);
+    else
+        Z = fft_run_smem<-1, false>(RowLoader{out, rs, row0, nrows}, sm, sb, plan, g, tw);
+    for (int e = threadIdx.x; e < NR * (M + 1); e += blockDim.x) {
+        const int l = (int)fdiv((unsigned)e, m1div), k = e - l * (M + 1);
         const long long row = row0 + l;
         if (row >= nrows) continue;
-        const float2 a = Z[l * ls + (k == M ? 0 : k)];
-        const float2 b = cconj(Z[l * ls + (k == 0 ? 0 : M - k)]);
+        const float2 a = Z[l * ls + spad(k == M ? 0 : k)];
+        const float2 b = cconj(Z[l * ls + spad(k == 0 ? 0 : M - k)]);
         const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
         const float2 D = csub(a, b);
         const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // (a-b)/(2i)
-        out[row * P + k] = cadd(E, cmul(__ldg(&tw[k]), O));
+        out[row * rs + k] = cadd(E, cmul(__ldg(&tw[k]), O));
     }
 }
 
 // ---------------------------------------------------------------------------
-// z pass, inverse c2r (unnormalised).  Z[k] = (X[k] + conj X[M-k]) +
-// i (X[k] - conj X[M-k]) W^-k, z = IFFT_M(Z), x[2m] = Re z[m], x[2m+1] = Im z[m].
-// Im X[0] and Im X[M] are ignored (as for a Hermitian spectrum).  Output goes
-// to the real view of `data` (GENERIC = false) or to out[row*opitch + z]*oscale.
+// z pass, inverse c2r (unnormalised): the pre-processing runs inside the first
+// pass's loads and the last pass writes the real row.
 // ---------------------------------------------------------------------------
 template <bool GENERIC>
-__global__ void k_fft_z_c2r(float2* data, int n, int P, long long nrows, int NR, FftPlan plan,
+__global__ void k_fft_z_c2r(float2* data, int n, long long rs, long long nrows, int NR, FftPlan plan,
                             const float2* __restrict__ tw, float* out, long long opitch, float oscale) {
     extern __shared__ float2 sm[];
     const int M = n / 2;
-    const int ls = M + 2;
+    const int ls = spad(M) + 1;
     float2* sb = sm + NR * ls;
     const long long row0 = (long long)blockIdx.x * NR;
-    const int T = blockDim.x;
-    for (int e = threadIdx.x; e < NR * (M + 1); e += T) {
-        const int l = e / (M + 1), k = e - l * (M + 1);
-        const long long row = row0 + l;
-        float2 v = make_float2(0.f, 0.f);
-        if (row < nrows) v = data[row * P + k];
-        if (k == 0 || k == M) v.y = 0.f;
-        sm[l * ls + k] = v;
-    }
-    __syncthreads();
-    const int H = M / 2 + 1;  // pairs (k, M-k) for k = 0 .. M/2
-    for (int e = threadIdx.x; e < NR * H; e += T) {
-        const int l = e / H, k = e - l * H;
-        float2* s = sm + l * ls;
-        if (k == 0) {
-            const float2 x0 = s[0], xm = s[M];
-            s[0] = make_float2(x0.x + xm.x, x0.x - xm.x);
-        } else {
-            const float2 xk = s[k], xmk = s[M - k];
-            float2 w = __ldg(&tw[k]);
-            w.y = -w.y;  // W^-k
-            {
-                const float2 a = xk, b = cconj(xmk);
-                const float2 d = cmul(csub(a, b), w);
-                s[k] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
-            }
-            if (M - k != k) {
-                float2 w2 = __ldg(&tw[M - k]);
-                w2.y = -w2.y;
-                const float2 a = xmk, b = cconj(xk);
-                const float2 d = cmul(csub(a, b), w2);
-                s[M - k] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
-            }
-        }
-    }
-    __syncthreads();
-    const float2* Zr = fft_smem(sm, sb, plan, NR, ls, 1, false, tw, 2, +1);
-    for (int e = threadIdx.x; e < NR * M; e += T) {
-        const int l = e / M, m = e - l * M;
-        const long long row = row0 + l;
-        if (row >= nrows) continue;
-        const float2 z = Zr[l * ls + m];
-        if (GENERIC) {
-            out[row * opitch + 2 * m] = z.x * oscale;
-            out[row * opitch + 2 * m + 1] = z.y * oscale;
-        } else {
-            data[row * P + m] = z;
-        }
-    }
+    const FftGeom g{NR, ls, 1, false, 0, 2};
+    const C2rLoader in{data, rs, M, row0, nrows, tw};
+    if (GENERIC)
+        fft_run_out<+1, false>(in, RowStoreGeneric{out, opitch, oscale, row0, nrows}, sm, sb, plan, g, tw);
+    else
+        fft_run_out<+1, false>(in, RowStore{data, rs, row0, nrows}, sm, sb, plan, g, tw);
 }
 
 // ---------------------------------------------------------------------------
 // strided complex pass along y (S = P, outer = ix) or x (S = n P, outer = iy):
-// a block transforms B adjacent kz columns of one outer index.
+// a block transforms B adjacent kz columns of one outer index, reading and
+// writing global memory in its first and last passes.  Tiles never cross the
+// padded row pitch P (a multiple of 16), so pad columns past n/2+1 are
+// transformed too: no kernel reads them as data.
 // ---------------------------------------------------------------------------
-__global__ void k_fft_strided(float2* data, int n, long long S, long long outer_stride, int ncols, int B, int nct,
-                              FftPlan plan, const float2* __restrict__ tw, int sign) {
+template <int SIGN>
+__global__ void k_fft_strided(float2* data, int n, LineGeom lg, int B, int nct, int ntiles, FftPlan plan,
+                              const float2* __restrict__ tw) {
+    const long long S = lg.S;
     extern __shared__ float2 sm[];
-    const long long o = blockIdx.x / nct;
-    const int ct = blockIdx.x - (int)(o * nct);
-    const int col0 = ct * B;
-    float2* base = data + o * outer_stride + col0;
-    const int T = blockDim.x;
-    for (int e = threadIdx.x; e < n * B; e += T) {
-        const int i = e / B, c = e - i * B;
-        sm[e] = (col0 + c < ncols) ? base[i * S + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const float2* R = fft_smem(sm, sm + n * B, plan, B, 1, B, true, tw, 1, sign);
-    for (int e = threadIdx.x; e < n * B; e += T) {
-        const int i = e / B, c = e - i * B;
-        if (col0 + c < ncols) base[i * S + c] = R[e];
+    const int tsz = spad(n) * B;
+    float2* stg = sm;  // prefetched raw tile
+    float2* A = sm + tsz;
+    float2* Bf = A + tsz;
+    float2* tws = Bf + tsz;  // twiddle table, copied once per persistent block
+    for (int q = threadIdx.x; q < n; q += blockDim.x) tws[q] = __ldg(tw + q);
+    const FftGeom g{B, 1, B, true, __ffs(B) - 1, 1};
+    auto tile_base = [&](int t) {
+        const int o = t / nct;
+        const int ct = t - o * nct;
+        const int o1 = o / lg.o2n, o2 = o - o1 * lg.o2n;
+        return data + o1 * lg.s1 + o2 * lg.s2 + ct * B;
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) tile_prefetch(stg, tile_base(t), n, B, S);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int tn = t + gridDim.x;
+        auto prefetch_next = [&]() {
+            if (tn < ntiles) tile_prefetch(stg, tile_base(tn), n, B, S);
+        };
+        fft_run_out<SIGN, true>(SmemIO{stg, 1, B}, ColIO{tile_base(t), S}, A, Bf, plan, g, tws, prefetch_next);
     }
 }
 
 // ---------------------------------------------------------------------------
 // x pass fused with the Poisson solve and gradient (Sec. 2.2; Eq. 2 force):
-// forward x FFT of delta_k, Phi_k = -green delta_k / k^2 (0 at k = 0), then for
-// each component F_j,k = -i k_j Phi_k (k_j = 0 on axis j's Nyquist plane) and
-// its inverse x FFT.  gscale = green / n^3 carries the c2r normalisation.
+// forward x FFT of delta_k, Phi_k = -green delta_k / k^2 (0 at k = 0), and the
+// force components F_j,k = -i k_j Phi_k (k_j = 0 on axis j's Nyquist plane)
+// brought back along x.  gscale = green / n^3 carries the c2r normalisation,
+// so with phi = gscale delta_k / k^2 (kept in registers), F_j = i k_j phi.
+// Two inverse transforms per tile: i k_x phi for the x component, and phi
+// itself, whose transform is scaled by i k_y and i k_z on the way out.  The
+// next tile's delta_k is prefetched with cp.async while this one is computed.
 // ---------------------------------------------------------------------------
-constexpr int kGreenEpt = 8;  // spectrum values each thread keeps in registers
+constexpr int kGreenEpt = 12;  // spectrum values each thread keeps in registers
 
-__global__ void __launch_bounds__(768) k_fft_x_green(const float2* __restrict__ mk, float2* f0, float2* f1, float2* f2, int n, int P,
-                              int B, int nct, FftPlan plan, const float2* __restrict__ tw, float gscale, float kf) {
+__global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f0, float2* f1, float2* f2,
+                                                     int n, long long RS, int B, int nct, int ntiles, FftPlan plan,
+                                                     const float2* __restrict__ tw, float gscale, float kf) {
     extern __shared__ float2 sm[];
-    float2* A = sm;
-    float2* W = sm + n * B;
-    const int iy = blockIdx.x / nct;
-    const int ct = blockIdx.x - iy * nct;
-    const int col0 = ct * B;
-    const int ncols = n / 2 + 1;
-    const long long S = (long long)n * P;
-    const long long off = (long long)iy * P + col0;
+    const int tsz = spad(n) * B;
+    float2* stg = sm;
+    float2* A = sm + tsz;
+    float2* W = A + tsz;
+    float2* tws = W + tsz;  // twiddle table, copied once per persistent block
+    for (int q = threadIdx.x; q < n; q += blockDim.x) tws[q] = __ldg(tw + q);
+    const long long S = (long long)n * RS;  // x stride; RS = stride of the y index
     const int T = blockDim.x;
-    for (int e = threadIdx.x; e < n * B; e += T) {
-        const int i = e / B, c = e - i * B;
-        A[e] = (col0 + c < ncols) ? mk[off + i * S + c] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const float2* X = fft_smem(A, W, plan, B, 1, B, true, tw, 1, -1);
-    // phi_e = green delta_k / (n^3 k^2) kept in registers: F_j,k = -i k_j Phi_k = i k_j phi
+    const int bs = __ffs(B) - 1;
     const int half = n / 2;
-    const float ky = kf * (float)(iy < half ? iy : iy - n);
-    float2 phi[kGreenEpt];
-#pragma unroll
-    for (int q = 0; q < kGreenEpt; ++q) {
-        const int e = threadIdx.x + q * T;
-        phi[q] = make_float2(0.f, 0.f);
-        if (e < n * B) {
-            const int i = e / B, c = e - i * B;
-            const float kx = kf * (float)(i < half ? i : i - n);
-            const float kz = kf * (float)(col0 + c);
-            const float k2 = kx * kx + ky * ky + kz * kz;
-            phi[q] = cscale(X[e], k2 > 0.f ? gscale / k2 : 0.f);
-        }
-    }
-    __syncthreads();
-    for (int j = 0; j < 3; ++j) {
+    const FftGeom g{B, 1, B, true, bs, 1};
+    auto tile_off = [&](int t) {
+        const int iy = t / nct;
+        const int ct = t - iy * nct;
+        return (long long)iy * RS + ct * B;
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) tile_prefetch(stg, mk + tile_off(t), n, B, S);
+    for (; t < ntiles; t += gridDim.x) {
+        const int iy = t / nct;
+        const int col0 = (t - iy * nct) * B;
+        const long long off = (long long)iy * RS + col0;
+        cp_async_wait_all();
+        __syncthreads();
+        const int tn = t + gridDim.x;
+        auto prefetch_next = [&]() {
+            if (tn < ntiles) tile_prefetch(stg, mk + tile_off(tn), n, B, S);
+        };
+        const float2* X = fft_run_smem<-1, true>(SmemIO{stg, 1, B}, A, W, plan, g, tws, prefetch_next);
+        const float ky = kf * (float)(iy < half ? iy : iy - n);
+        float2 phi[kGreenEpt];
 #pragma unroll
         for (int q = 0; q < kGreenEpt; ++q) {
             const int e = threadIdx.x + q * T;
+            phi[q] = make_float2(0.f, 0.f);
             if (e < n * B) {
-                const int i = e / B, c = e - i * B;
-                float kj;
-                if (j == 0)
-                    kj = (i == half) ? 0.f : kf * (float)(i < half ? i : i - n);
-                else if (j == 1)
-                    kj = (iy == half) ? 0.f : ky;
-                else
-                    kj = (col0 + c == half) ? 0.f : kf * (float)(col0 + c);
-                A[e] = make_float2(-kj * phi[q].y, kj * phi[q].x);  // i k_j phi
+                const int i = e >> bs, c = e & (B - 1);
+                const float kx = kf * (float)(i < half ? i : i - n);
+                const float kz = kf * (float)(col0 + c);
+                const float k2 = kx * kx + ky * ky + kz * kz;
+                phi[q] = cscale(X[c + spad(i) * B], k2 > 0.f ? gscale / k2 : 0.f);
             }
         }
         __syncthreads();
-        const float2* R = fft_smem(A, W, plan, B, 1, B, true, tw, 1, +1);
-        float2* dst = (j == 0 ? f0 : (j == 1 ? f1 : f2)) + off;
-        for (int e = threadIdx.x; e < n * B; e += T) {
-            const int i = e / B, c = e - i * B;
-            if (col0 + c < ncols) dst[i * S + c] = R[e];
+        const float ky_eff = (iy == half) ? 0.f : ky;
+        for (int j = 0; j < 2; ++j) {
+            // j = 0: x component, IFFT_x(i k_x phi); j = 1: Psi = IFFT_x(phi) for y and z
+#pragma unroll
+            for (int q = 0; q < kGreenEpt; ++q) {
+                const int e = threadIdx.x + q * T;
+                if (e < n * B) {
+                    const int i = e >> bs, c = e & (B - 1);
+                    if (j == 0) {
+                        const float kx = (i == half) ? 0.f : kf * (float)(i < half ? i : i - n);
+                        A[c + spad(i) * B] = make_float2(-kx * phi[q].y, kx * phi[q].x);  // i k_x phi
+                    } else {
+                        A[c + spad(i) * B] = phi[q];
+                    }
+                }
+            }
+            __syncthreads();
+            if (j == 0)
+                fft_run_out<+1, true>(SmemIO{A, 1, B}, ColIO{f0 + off, S}, W, A, plan, g, tws);
+            else
+                fft_run_out<+1, true>(SmemIO{A, 1, B}, YZStore{f1 + off, f2 + off, S, ky_eff, kf, col0, half}, W, A,
+                                      plan, g, tws);
         }
-        __syncthreads();
     }
 }
 
@@ -278,42 +417,53 @@ static bool set_smem(const void* fn, size_t bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
-int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s) {
+// threads: about one butterfly of the first (largest-radix) pass per thread
+static int pass_threads(const FftPlan& plan, long lines) {
+    long t = plan.n / plan.radix[0] * lines;
+    t = (t + 31) / 32 * 32;
+    if (t < 128) t = 128;
+    if (t > 256) t = 256;
+    return (int)t;
+}
+
+int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,
+              long long rs, long long nrows) {
     FftPlan plan;
     if (!make_plan(n / 2, &plan)) return COLA_EUNSUPPORTED_SIZE;
-    const int M = n / 2, P = fft_pitch(n);
+    const int M = n / 2;
     const int NR = z_rows_per_block(M);
-    const long long nrows = (long long)n * n;
-    const int T = round_threads((long)NR * M);
-    const size_t smem = (size_t)2 * NR * (M + 1) * 8;
+    const int T = pass_threads(plan, NR);
+    const size_t smem = (size_t)2 * NR * (spad(M) + 1) * 8;
     const long long grid = (nrows + NR - 1) / NR;
     ProfScope ps(dep ? kKZr2cFix : kKZr2c, s);
     if (dep) {
         if (!set_smem((const void*)k_fft_z_r2c<true>, smem)) return COLA_ECUDA;
-        k_fft_z_r2c<true><<<(unsigned)grid, T, smem, s>>>(dep, out, n, P, nrows, NR, scale, plan, tw);
+        k_fft_z_r2c<true><<<(unsigned)grid, T, smem, s>>>(dep, out, n, rs, nrows, NR, scale, plan, tw,
+                                                           make_fastdiv(M + 1));
     } else {
         if (!set_smem((const void*)k_fft_z_r2c<false>, smem)) return COLA_ECUDA;
-        k_fft_z_r2c<false><<<(unsigned)grid, T, smem, s>>>(nullptr, out, n, P, nrows, NR, 0.f, plan, tw);
+        k_fft_z_r2c<false><<<(unsigned)grid, T, smem, s>>>(nullptr, out, n, rs, nrows, NR, 0.f, plan, tw,
+                                                            make_fastdiv(M + 1));
     }
     return check_launch();
 }
 
-int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale) {
+int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale,
+              long long rs, long long nrows) {
     FftPlan plan;
     if (!make_plan(n / 2, &plan)) return COLA_EUNSUPPORTED_SIZE;
-    const int M = n / 2, P = fft_pitch(n);
+    const int M = n / 2;
     const int NR = z_rows_per_block(M);
-    const long long nrows = (long long)n * n;
-    const int T = round_threads((long)NR * M);
-    const size_t smem = (size_t)2 * NR * (M + 2) * 8;
+    const int T = pass_threads(plan, NR);
+    const size_t smem = (size_t)2 * NR * (spad(M) + 1) * 8;
     const long long grid = (nrows + NR - 1) / NR;
     ProfScope ps(kKZc2r, s);
     if (out) {
         if (!set_smem((const void*)k_fft_z_c2r<true>, smem)) return COLA_ECUDA;
-        k_fft_z_c2r<true><<<(unsigned)grid, T, smem, s>>>(data, n, P, nrows, NR, plan, tw, out, opitch, oscale);
+        k_fft_z_c2r<true><<<(unsigned)grid, T, smem, s>>>(data, n, rs, nrows, NR, plan, tw, out, opitch, oscale);
     } else {
         if (!set_smem((const void*)k_fft_z_c2r<false>, smem)) return COLA_ECUDA;
-        k_fft_z_c2r<false><<<(unsigned)grid, T, smem, s>>>(data, n, P, nrows, NR, plan, tw, nullptr, 0, 1.f);
+        k_fft_z_c2r<false><<<(unsigned)grid, T, smem, s>>>(data, n, rs, nrows, NR, plan, tw, nullptr, 0, 1.f);
     }
     return check_launch();
 }
@@ -321,39 +471,66 @@ int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out,
 // adjacent kz columns per block: two ping-pong buffers of n*B complex each
 static int strided_cols(int n) { return n <= 256 ? 16 : (n <= 768 ? 8 : (n <= 2048 ? 4 : 2)); }
 
-int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaStream_t s) {
+static int g_num_sms = 0;
+static int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_num_sms = 132;
+    }
+    return g_num_sms;
+}
+
+// Persistent blocks: three tile buffers (prefetch + ping-pong), blocks per SM
+// from the shared-memory budget.
+static int persistent_grid(size_t smem, int ntiles) {
+    int per_sm = (int)((227 * 1024) / (smem + 1024));
+    if (per_sm < 1) per_sm = 1;
+    int grid = num_sms() * per_sm;
+    return grid < ntiles ? grid : ntiles;
+}
+
+int fft_lines(float2* data, int n, int sign, const float2* tw, cudaStream_t s, LineGeom lg, int kid) {
     FftPlan plan;
     if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
-    const int P = fft_pitch(n);
     const int B = strided_cols(n);
-    const int ncols = n / 2 + 1;
-    const int nct = (ncols + B - 1) / B;
-    const long long S = axis == 1 ? P : (long long)n * P;
-    const long long outer_stride = axis == 1 ? (long long)n * P : P;
-    const int T = round_threads((long)n * B);
-    const size_t smem = (size_t)2 * n * B * 8;
-    if (!set_smem((const void*)k_fft_strided, smem)) return COLA_ECUDA;
-    ProfScope ps(axis == 1 ? (sign < 0 ? kKYFwd : kKYInv) : (sign < 0 ? kKXFwd : kKXInv), s);
-    k_fft_strided<<<(unsigned)(n * nct), T, smem, s>>>(data, n, S, outer_stride, ncols, B, nct, plan, tw, sign);
+    const int nct = (n / 2 + 1 + B - 1) / B;
+    const long long ntl = (long long)lg.nouter * nct;
+    if (ntl > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
+    const int ntiles = (int)ntl;
+    int T = pass_threads(plan, B) * 2;
+    const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
+    auto kern = sign < 0 ? k_fft_strided<-1> : k_fft_strided<+1>;
+    if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
+    ProfScope ps(kid, s);
+    kern<<<persistent_grid(smem, ntiles), T, smem, s>>>(data, n, lg, B, nct, ntiles, plan, tw);
     return check_launch();
 }
 
-int fft_x_green(const float2* mk, float2* f0, float2* f1, float2* f2, int n, float gscale, float kf,
-                const float2* tw, cudaStream_t s) {
+int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaStream_t s) {
+    const long long P = fft_pitch(n);
+    const LineGeom lg = axis == 1 ? LineGeom{P, n, 1, (long long)n * P, 0} : LineGeom{(long long)n * P, n, 1, P, 0};
+    return fft_lines(data, n, sign, tw, s, lg,
+                     axis == 1 ? (sign < 0 ? kKYFwd : kKYInv) : (sign < 0 ? kKXFwd : kKXInv));
+}
+
+int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s) {
     FftPlan plan;
     if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
-    const int P = fft_pitch(n);
+    const long long P = fft_pitch(n);
     int B = strided_cols(n);
-    while (B > 1 && n * B > 768 * kGreenEpt) B /= 2;
-    const int ncols = n / 2 + 1;
-    const int nct = (ncols + B - 1) / B;
+    while (B > 2 && n * B > 512 * kGreenEpt) B /= 2;
+    const int nct = (n / 2 + 1 + B - 1) / B;
+    const int ntiles = n * nct;
     int T = ((n * B + kGreenEpt - 1) / kGreenEpt + 31) / 32 * 32;
     if (T < 64) T = 64;
-    if (T > 768) return COLA_EUNSUPPORTED_SIZE;
-    const size_t smem = (size_t)2 * n * B * 8;
+    if (T > 512) return COLA_EUNSUPPORTED_SIZE;
+    const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
     if (!set_smem((const void*)k_fft_x_green, smem)) return COLA_ECUDA;
     ProfScope ps(kKXGreen, s);
-    k_fft_x_green<<<(unsigned)(n * nct), T, smem, s>>>(mk, f0, f1, f2, n, P, B, nct, plan, tw, gscale, kf);
+    // interleaved force mesh: rows (ix, iy, c) of P complex, delta_k in c = 0
+    k_fft_x_green<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, F, F + P, F + 2 * P, n, 3 * P, B, nct, ntiles,
+                                                                  plan, tw, gscale, kf);
     return check_launch();
 }
 

@@ -19,9 +19,6 @@
 
 namespace cola {
 
-int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s);
-int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale);
-int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaStream_t s);
 
 struct CosmoD {
     double om, ol, ok, ob, h, s8, ns, tcmb;
@@ -394,7 +391,8 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
         k_noise<<<gr, 256, 0, s>>>(reinterpret_cast<float*>(b[0]), nq, 2ll * P, seed);
     }
     if ((rc = check_launch())) return rc;
-    if ((rc = fft_z_r2c(nullptr, b[0], nq, 0.f, tw, s))) return rc;
+    const long long nrows = (long long)nq * nq;
+    if ((rc = fft_z_r2c(nullptr, b[0], nq, 0.f, tw, s, P, nrows))) return rc;
     if ((rc = fft_strided(b[0], nq, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(b[0], nq, 0, -1, tw, s))) return rc;
     {
@@ -407,8 +405,8 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
         int r;
         if ((r = fft_strided(buf, nq, 0, +1, tw, s))) return r;
         if ((r = fft_strided(buf, nq, 1, +1, tw, s))) return r;
-        if (out) return fft_z_c2r(buf, nq, tw, s, out, nq, 1.f);
-        return fft_z_c2r(buf, nq, tw, s, nullptr, 0, 1.f);
+        if (out) return fft_z_c2r(buf, nq, tw, s, out, nq, 1.f, P, nrows);
+        return fft_z_c2r(buf, nq, tw, s, nullptr, 0, 1.f, P, nrows);
     };
     // Psi1
     for (int a = 0; a < 3; ++a) {
@@ -436,7 +434,7 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
                                        (const float*)b[5], (const float*)b[6], nq, 2ll * P);
     }
     if ((rc = check_launch())) return rc;
-    if ((rc = fft_z_r2c(nullptr, b[1], nq, 0.f, tw, s))) return rc;
+    if ((rc = fft_z_r2c(nullptr, b[1], nq, 0.f, tw, s, P, nrows))) return rc;
     if ((rc = fft_strided(b[1], nq, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(b[1], nq, 0, -1, tw, s))) return rc;
     for (int a = 0; a < 3; ++a) {

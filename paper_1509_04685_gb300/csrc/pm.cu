@@ -113,10 +113,11 @@ int launch_deposit_ex(const float* d, const float* v, const float* psi1, const f
 }
 
 // --------------------------------------------------------------------------
-// CIC interpolation of the three force meshes (real view, row pitch P2 floats)
+// CIC interpolation of the three force components from the interleaved force
+// mesh (real view): component j of cell (ix, iy, z) at ((ix ng + iy) 3 + j) P2 + z,
+// P2 = 2P floats, so the three components of a cell are P2 apart.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void gather3(const float* __restrict__ f0, const float* __restrict__ f1,
-                                        const float* __restrict__ f2, int ng, long long P2, const Cic& c,
+__device__ __forceinline__ void gather3(const float* __restrict__ Fm, int ng, long long P2, const Cic& c,
                                         float F[3]) {
     F[0] = F[1] = F[2] = 0.f;
     const int ix[2] = {c.c0[0], c.c1[0]};
@@ -129,22 +130,21 @@ __device__ __forceinline__ void gather3(const float* __restrict__ f0, const floa
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const long long row = ((long long)ix[a] * ng + iy[b]) * P2;
+            const long long row = ((long long)ix[a] * ng + iy[b]) * 3 * P2;
             const float wab = wx[a] * wy[b];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const float w = wab * wz[e];
                 const long long q = row + iz[e];
-                F[0] += w * __ldg(f0 + q);
-                F[1] += w * __ldg(f1 + q);
-                F[2] += w * __ldg(f2 + q);
+                F[0] += w * __ldg(Fm + q);
+                F[1] += w * __ldg(Fm + q + P2);
+                F[2] += w * __ldg(Fm + q + 2 * P2);
             }
         }
 }
 
-__global__ void k_gather(const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ f2,
-                         const float* __restrict__ d, float* __restrict__ out, int nq, int ng, long long P2,
-                         float inv_cell, long long np) {
+__global__ void k_gather(const float* __restrict__ Fm, const float* __restrict__ d, float* __restrict__ out, int nq,
+                         int ng, long long P2, float inv_cell, long long np) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     float dx[3] = {d[p], d[np + p], d[2 * np + p]};
@@ -154,19 +154,18 @@ __global__ void k_gather(const float* __restrict__ f0, const float* __restrict__
         return;
     }
     float F[3];
-    gather3(f0, f1, f2, ng, P2, c, F);
+    gather3(Fm, ng, P2, c, F);
     out[p] = F[0];
     out[np + p] = F[1];
     out[2 * np + p] = F[2];
 }
 
-int launch_gather(const float2* f0, const float2* f1, const float2* f2, const float* d, float* out, int nq, int ng,
-                  double box, cudaStream_t s) {
+int launch_gather(const float2* Fm, const float* d, float* out, int nq, int ng, double box, cudaStream_t s) {
     const long long np = (long long)nq * nq * nq;
     const int T = 256;
     ProfScope ps(kKGather, s);
-    k_gather<<<(unsigned)((np + T - 1) / T), T, 0, s>>>((const float*)f0, (const float*)f1, (const float*)f2, d, out,
-                                                         nq, ng, 2ll * fft_pitch(ng), (float)((double)ng / box), np);
+    k_gather<<<(unsigned)((np + T - 1) / T), T, 0, s>>>((const float*)Fm, d, out, nq, ng, 2ll * fft_pitch(ng),
+                                                         (float)((double)ng / box), np);
     return check_launch();
 }
 
@@ -176,8 +175,7 @@ int launch_gather(const float2* f0, const float2* f1, const float2* f2, const fl
 //   A = F - c1 psi1 - c2 psi2;  v += kick A;  (not last) d += drift v + dD1 psi1 + dD2 psi2
 // PM-only (App. B): A = F, d += drift v.
 // --------------------------------------------------------------------------
-__global__ void k_gather_kick_drift(const float* __restrict__ f0, const float* __restrict__ f1,
-                                    const float* __restrict__ f2, float* __restrict__ d, float* __restrict__ v,
+__global__ void k_gather_kick_drift(const float* __restrict__ Fm, float* __restrict__ d, float* __restrict__ v,
                                     const float* __restrict__ psi1, const float* __restrict__ psi2,
                                     const double* __restrict__ row, int nq, int ng, long long P2, float inv_cell,
                                     long long np, int last, int pm_only, int* status) {
@@ -192,7 +190,7 @@ __global__ void k_gather_kick_drift(const float* __restrict__ f0, const float* _
         return;
     }
     float F[3];
-    gather3(f0, f1, f2, ng, P2, c, F);
+    gather3(Fm, ng, P2, c, F);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const long long q = a * np + p;
@@ -204,13 +202,13 @@ __global__ void k_gather_kick_drift(const float* __restrict__ f0, const float* _
     }
 }
 
-int launch_gather_kick_drift(const float2* f0, const float2* f1, const float2* f2, cola_state st, const double* row,
-                             int nq, int ng, double box, int last, int pm_only, int* status, cudaStream_t s) {
+int launch_gather_kick_drift(const float2* Fm, cola_state st, const double* row, int nq, int ng, double box, int last,
+                             int pm_only, int* status, cudaStream_t s) {
     const long long np = (long long)nq * nq * nq;
     const int T = 256;
     ProfScope ps(kKGatherKD, s);
     k_gather_kick_drift<<<(unsigned)((np + T - 1) / T), T, 0, s>>>(
-        (const float*)f0, (const float*)f1, (const float*)f2, st.d, st.v, st.psi1, st.psi2, row, nq, ng,
+        (const float*)Fm, st.d, st.v, st.psi1, st.psi2, row, nq, ng,
         2ll * fft_pitch(ng), (float)((double)ng / box), np, last, pm_only, status);
     return check_launch();
 }

@@ -15,7 +15,7 @@ namespace cola {
 constexpr int kPkBlocks = 608;  // 4 blocks per SM on a 152-SM GB300
 constexpr int kPkThreads = 256;
 
-__global__ void k_pk_shells(const float2* __restrict__ mk, int ng, int P, float amp_scale, float kf, int flags,
+__global__ void k_pk_shells(const float2* __restrict__ mk, int ng, long long P, float amp_scale, float kf, int flags,
                             int nbins, double* __restrict__ part) {
     extern __shared__ float bins[];  // 3 x nbins: sum w, sum w k, sum w P
     for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) bins[i] = 0.f;
@@ -90,7 +90,7 @@ __global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nb
     pk[i] = w > 0.0 ? wp / w : 0.0;
 }
 
-int launch_power(const float2* mk, int ng, double box, int flags, double* part, double* k, double* pk,
+int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
                  double* nmodes, int nbins, cudaStream_t s) {
     const double ng3 = (double)ng * ng * ng;
     const float amp_scale = (float)(box * sqrt(box) / ng3);  // sqrt(L^3 / ng^6)
@@ -101,7 +101,7 @@ int launch_power(const float2* mk, int ng, double box, int flags, double* part, 
         return COLA_ECUDA;
     {
         ProfScope ps(kKPkShells, s);
-        k_pk_shells<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, fft_pitch(ng), amp_scale, kf, flags, nbins, part);
+        k_pk_shells<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, flags, nbins, part);
     }
     int rc = check_launch();
     if (rc) return rc;
