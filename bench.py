@@ -240,9 +240,6 @@ def main():
     nk = C.LIB.cola_num_kernel_ids()
     launches0 = C.cola_launch_count()
     import ctypes
-    C.LIB.cola_profile_start.argtypes = [ctypes.c_int32]
-    C.LIB.cola_profile_stop.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
-    C.LIB.cola_kernel_name.restype = ctypes.c_char_p
     C.LIB.cola_profile_start(args.steps * 16 + 64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

@@ -51,6 +51,7 @@ extern "C" {
 #define COLA_SAMPLING_POW 2    /* f(a) = a^p, p = sampling_p */
 
 #define COLA_FLAG_PM_ONLY 1u /* App. B: plain PM, no LPT frame (v holds the full momentum) */
+#define COLA_FLAG_LEARNED 2u /* force = filtered coarse PM force + conv-net residual (cfg->net) */
 
 #define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.4) */
 #define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.4) */
@@ -60,6 +61,26 @@ typedef struct cola_cosmology {
     double omega_m, omega_l, omega_b, h, sigma8, n_s;
     double t_cmb; /* K, used by the Eisenstein & Hu no-wiggle transfer function */
 } cola_cosmology;
+
+/* Learned coarse-mesh force correction (not in the paper; used with
+ * COLA_FLAG_LEARNED, typically on a PM_grid = 1 mesh).  The force mesh is
+ *   F = IFFT(T(|k|) F_k) + g net(delta, F/g),   g = 3/2 Om/a,
+ * with T a radial transfer function (piecewise linear on nfilter nodes
+ * k_b = b sqrt(3) pi ng / (L (nfilter - 1)); NULL means T = 1) and net three
+ * circular 3x3x3 convolutions 4 -> 16 -> 16 -> 3 with ReLU, BF16 weights and
+ * activations, FP32 accumulation.  params (device, FP32, COLA_NET_NPARAMS):
+ *   W1 [16][4][27] @0, b1 [16] @1728, W2 [16][16][27] @1744, b2 [16] @8656,
+ *   W3 [3][16][27] @8672, b3 [3] @9968   (tap t = 9 tx + 3 ty + tz reads x[v + t - 1]).
+ * wpack (device, COLA_NET_NPACK bf16 values) holds the packed weights that
+ * cola_net_pack writes from params; call it after every change of params. */
+#define COLA_NET_NPARAMS 9971
+#define COLA_NET_NPACK 31104
+typedef struct cola_net {
+    float* params;
+    void* wpack;
+    const float* filter;
+    int32_t nfilter;
+} cola_net;
 
 /* One simulation (Table 1's code parameters). */
 typedef struct cola_config {
@@ -73,6 +94,7 @@ typedef struct cola_config {
     double sampling_p;  /* exponent for COLA_SAMPLING_POW */
     uint32_t flags;     /* COLA_FLAG_* */
     cola_cosmology cosmo;
+    const cola_net* net; /* host pointer, required with COLA_FLAG_LEARNED (ng a multiple of 16) */
 } cola_config;
 
 /* Particle state: four SoA float[3*Np] device arrays.
@@ -152,6 +174,33 @@ int cola_status(void* ws, size_t ws_bytes, void* stream);
 /* Number of kernels this library launched since load (a counter the host
  * side increments per launch). */
 uint64_t cola_launch_count(void);
+
+/* Write the packed BF16 weights of `net` from its FP32 parameters. */
+int cola_net_pack(const cola_net* net, void* stream);
+
+/* Gradient of the particle loss of the learned force (COLA_FLAG_LEARNED):
+ *   L = 1/(2 Np) sum_p |F(p) - target(p)|^2
+ * at scale factor a, through the CIC gather adjoint (a deposit of the
+ * residuals) and the three convolutions.  target: device SoA float[3*Np];
+ * grad: device float[COLA_NET_NPARAMS] (overwritten, W and b of all layers);
+ * loss: device double[1]. */
+int cola_net_grad(const cola_config* cfg, const cola_state* st, double a, const float* target, float* grad,
+                  double* loss, void* ws, size_t ws_bytes, void* stream);
+
+/* Adam step on n device floats: m, v moments, step t >= 1 (bias correction). */
+int cola_adam(float* params, const float* grad, float* m, float* v, int32_t n, int32_t t, float lr, float beta1,
+              float beta2, float eps, void* stream);
+
+/* Normal equations of the radial filter fit (linear least squares: the
+ * gathered force is linear in T).  For each hat basis function b < nb the
+ * filtered coarse force G(IFFT(e_b(|k|) F_k)) at the particles forms column b;
+ * ATA (nb*nb) and ATy (nb), device float64, are accumulated (not cleared) with
+ * y = target.  basis: device scratch of nb*3*Np floats. */
+int cola_filter_accumulate(const cola_config* cfg, const cola_state* st, double a, const float* target, int32_t nb,
+                           float* basis, double* ATA, double* ATy, void* ws, size_t ws_bytes, void* stream);
+
+/* Solve (ATA + ridge tr(ATA)/nb I) T = ATy (FP64 Cholesky on the device), T float[nb]. */
+int cola_filter_solve(const double* ATA, const double* ATy, int32_t nb, double ridge, float* T, void* stream);
 
 /* cola_density without any caller workspace, for callers that cannot hand the
  * library scratch memory: e.g. a host application whose device memory is all

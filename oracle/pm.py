@@ -89,14 +89,28 @@ def density_contrast(d, nq: int, ng: int, L: float) -> np.ndarray:
     return cic_deposit(u, ng) * (ng / nq) ** 3 - 1.0
 
 
-def force_mesh_from_delta(delta: np.ndarray, L: float, green: float) -> np.ndarray:
-    """(3, ng, ng, ng) force field F = -grad Phi, lap Phi = green * delta."""
+def radial_filter(kmag: np.ndarray, T: np.ndarray, kmax: float) -> np.ndarray:
+    """Piecewise-linear transfer function on nodes b * kmax / (len(T) - 1)
+    (the learned coarse-mesh filter; not in the paper)."""
+    nb = len(T)
+    u = kmag / (kmax / (nb - 1))
+    b = np.minimum(np.floor(u).astype(np.int64), nb - 2)
+    f = np.minimum(u - b, 1.0)
+    return (1.0 - f) * T[b] + f * T[b + 1]
+
+
+def force_mesh_from_delta(delta: np.ndarray, L: float, green: float, filt=None) -> np.ndarray:
+    """(3, ng, ng, ng) force field F = -grad Phi, lap Phi = green * delta; with
+    filt = T (node values) the potential is multiplied by the radial filter,
+    nodes spaced sqrt(3) pi ng / L / (len(T) - 1)."""
     ng = delta.shape[0]
     kx, ky, kz, nx, ny, nz = kgrid(ng, L)
     k2 = kx**2 + ky**2 + kz**2
     k2[0, 0, 0] = 1.0
     dk = np.fft.rfftn(delta)
     phik = -green * dk / k2
+    if filt is not None:
+        phik = phik * radial_filter(np.sqrt(k2), np.asarray(filt, dtype=np.float64), np.sqrt(3.0) * np.pi * ng / L)
     phik[0, 0, 0] = 0.0
     out = []
     for kj, nyq in ((kx, nx), (ky, ny), (kz, nz)):

@@ -19,6 +19,11 @@ ERRORS = {-1: "COLA_EINVAL", -2: "COLA_EWORKSPACE", -3: "COLA_EUNSUPPORTED_SIZE"
           -5: "COLA_ETIMEOUT", -6: "COLA_ENONFINITE"}
 SAMPLING_LINEAR, SAMPLING_LOG, SAMPLING_POW = 0, 1, 2
 FLAG_PM_ONLY = 1
+FLAG_LEARNED = 2
+NET_NPARAMS = 9971
+NET_NPACK = 31104
+NET_OFFSETS = {"W1": (0, (16, 4, 27)), "b1": (1728, (16,)), "W2": (1744, (16, 16, 27)), "b2": (8656, (16,)),
+               "W3": (8672, (3, 16, 27)), "b3": (9968, (3,))}
 PK_DECONV_CIC, PK_ALIAS_JING = 1, 2
 TABLE_COLUMNS = ("a", "green", "c1", "c2", "kick", "drift", "dD1", "dD2", "D1", "D2", "dD1da", "dD2da")
 
@@ -29,11 +34,16 @@ class cola_cosmology(ctypes.Structure):
                 ("t_cmb", ctypes.c_double)]
 
 
+class cola_net(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("wpack", ctypes.c_void_p), ("filter", ctypes.c_void_p),
+                ("nfilter", ctypes.c_int32)]
+
+
 class cola_config(ctypes.Structure):
     _fields_ = [("nq", ctypes.c_int32), ("ng", ctypes.c_int32), ("box", ctypes.c_double),
                 ("a_init", ctypes.c_double), ("a_final", ctypes.c_double), ("n_steps", ctypes.c_int32),
                 ("sampling", ctypes.c_int32), ("sampling_p", ctypes.c_double), ("flags", ctypes.c_uint32),
-                ("cosmo", cola_cosmology)]
+                ("cosmo", cola_cosmology), ("net", ctypes.POINTER(cola_net))]
 
 
 class cola_state(ctypes.Structure):
@@ -68,6 +78,16 @@ def _load():
         "cola_status": ([vp, sz, vp], ctypes.c_int),
         "cola_launch_count": ([], ctypes.c_uint64),
         "cola_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "cola_net_pack": ([ctypes.POINTER(cola_net), vp], ctypes.c_int),
+        "cola_net_grad": ([cfgp, stp, dbl, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+        "cola_adam": ([vp, vp, vp, vp, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp],
+                      ctypes.c_int),
+        "cola_filter_accumulate": ([cfgp, stp, dbl, vp, i32, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+        "cola_filter_solve": ([vp, vp, i32, dbl, vp, vp], ctypes.c_int),
+        "cola_profile_start": ([i32], ctypes.c_int),
+        "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
+        "cola_num_kernel_ids": ([], i32),
+        "cola_kernel_name": ([i32], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -105,9 +125,42 @@ def _stream(stream):
 
 def make_config(nq: int, ng: int, box: float, a_init: float, a_final: float = 1.0, n_steps: int = 40,
                 sampling: int = SAMPLING_LINEAR, sampling_p: float = 1.0, flags: int = 0,
-                omega_m=0.25, omega_l=0.75, omega_b=0.044, h=0.7, sigma8=0.8, n_s=0.95, t_cmb=2.7255):
+                omega_m=0.25, omega_l=0.75, omega_b=0.044, h=0.7, sigma8=0.8, n_s=0.95, t_cmb=2.7255, net=None):
     cosmo = cola_cosmology(omega_m, omega_l, omega_b, h, sigma8, n_s, t_cmb)
-    return cola_config(nq, ng, box, a_init, a_final, n_steps, sampling, sampling_p, flags, cosmo)
+    cfg = cola_config(nq, ng, box, a_init, a_final, n_steps, sampling, sampling_p, flags, cosmo,
+                      ctypes.pointer(net) if net is not None else None)
+    cfg._net_ref = net  # keep the descriptor alive with the config
+    return cfg
+
+
+def make_net(params, wpack, filt=None) -> cola_net:
+    """Descriptor of a learned correction: params (device float[NET_NPARAMS]),
+    wpack (device bf16[NET_NPACK] storage), optional filter table (device float[n])."""
+    return cola_net(_ptr(params), _ptr(wpack), _ptr(filt), 0 if filt is None else int(filt.numel()))
+
+
+def cola_net_pack(net: cola_net, stream=None):
+    _check(LIB.cola_net_pack(ctypes.byref(net), _stream(stream)), "cola_net_pack")
+
+
+def cola_net_grad(cfg, st: cola_state, a: float, target, grad, loss, ws, stream=None):
+    _check(LIB.cola_net_grad(ctypes.byref(cfg), ctypes.byref(st), a, _ptr(target), _ptr(grad), _ptr(loss), _ptr(ws),
+                             ws.numel() * ws.element_size(), _stream(stream)), "cola_net_grad")
+
+
+def cola_adam(params, grad, m, v, n: int, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(LIB.cola_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), n, t, lr, beta1, beta2, eps, _stream(stream)),
+           "cola_adam")
+
+
+def cola_filter_accumulate(cfg, st: cola_state, a: float, target, nb: int, basis, ATA, ATy, ws, stream=None):
+    _check(LIB.cola_filter_accumulate(ctypes.byref(cfg), ctypes.byref(st), a, _ptr(target), nb, _ptr(basis), _ptr(ATA),
+                                      _ptr(ATy), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "cola_filter_accumulate")
+
+
+def cola_filter_solve(ATA, ATy, nb: int, ridge: float, T, stream=None):
+    _check(LIB.cola_filter_solve(_ptr(ATA), _ptr(ATy), nb, ridge, _ptr(T), _stream(stream)), "cola_filter_solve")
 
 
 def make_state(d, v=None, psi1=None, psi2=None) -> cola_state:

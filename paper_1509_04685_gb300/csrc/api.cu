@@ -28,6 +28,11 @@ static int check_config(const cola_config* c) {
     const cola_cosmology& k = c->cosmo;
     if (!(k.omega_m > 0.0) || !(k.h > 0.0) || !(k.sigma8 > 0.0) || !(k.omega_b >= 0.0) || !(k.t_cmb > 0.0))
         return COLA_EINVAL;
+    if (c->flags & COLA_FLAG_LEARNED) {
+        if (c->ng % 16) return COLA_EUNSUPPORTED_SIZE;  // conv bricks of 4 x 8 x 16 voxels
+        if (!c->net || !c->net->params || !c->net->wpack) return COLA_EINVAL;
+        if (c->net->filter && (c->net->nfilter < 2 || c->net->nfilter > 64)) return COLA_EINVAL;
+    }
     return COLA_OK;
 }
 
@@ -39,6 +44,11 @@ bool layout_for(const cola_config* cfg, Layout* L) {
     L->ic = L->dep;
     L->pk_part = align_up(L->F + 2 * Mg, 4096);
     size_t end = L->F + 3 * Mg;
+    L->lrn = 0;
+    if (cfg->flags & COLA_FLAG_LEARNED) {
+        L->lrn = align_up(end, 4096);
+        end = L->lrn + learned_bytes(ng, nq);
+    }
     size_t ic_end = L->ic + 7 * Mq;
     size_t pk_end = L->pk_part + power_partial_bytes(ng / 2);
     if (ic_end > end) end = ic_end;
@@ -80,7 +90,7 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 // in component 0 until the x pass replaces it by F_x and adds F_y, F_z; the
 // inverse y and z passes then run over all three components in one launch each.
 static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
-                          cudaStream_t s) {
+                          cudaStream_t s, const float* filt = nullptr, int nfilt = 0, bool learned = false) {
     const int ng = cfg->ng, nq = cfg->nq;
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
     float2* F = reinterpret_cast<float2*>(wsp(ws, L.F));
@@ -92,12 +102,27 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     int rc;
     if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws), s)))
         return rc;
+    // the net's input keeps delta in real space (first buffer of the learned region)
+    if (learned && (rc = launch_fix_to_delta(dep, reinterpret_cast<float*>(wsp(ws, L.lrn)), ng, scale, s, false)))
+        return rc;
     if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, 3 * P, n2))) return rc;
     if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * P, ng, 1, ng * 3 * P, 0}, kKYFwd))) return rc;
-    if ((rc = fft_x_green(F, ng, (float)(green / ng3), (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s)))
+    const double kmax = std::sqrt(3.0) * 3.14159265358979323846 * ng / cfg->box;
+    if ((rc = fft_x_green(F, ng, (float)(green / ng3), (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s, filt,
+                          nfilt, nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f)))
         return rc;
     if ((rc = fft_lines(F, ng, +1, tw, s, LineGeom{3 * P, 3 * ng, 3, ng * 3 * P, P}, kKYInv))) return rc;
-    return fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2);
+    if ((rc = fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2))) return rc;
+    if (learned) return net_forward(cfg->net, wsp(ws, L.lrn), ng, nq, (float)green, F, s);
+    return COLA_OK;
+}
+
+static int pm_forces_for(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
+                         cudaStream_t s) {
+    if (cfg->flags & COLA_FLAG_LEARNED)
+        return pm_mesh_forces(cfg, st, green, ws, L, s, cfg->net->filter, cfg->net->filter ? cfg->net->nfilter : 0,
+                              true);
+    return pm_mesh_forces(cfg, st, green, ws, L, s);
 }
 
 static const float2* twiddles_for(int n, const cola_config* cfg, void* ws, cudaStream_t s, int* rc) {
@@ -159,7 +184,7 @@ int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float*
     if (!state_ok(st, false) || !force || !(a > 0.0)) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / a;
-    if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
     return launch_gather(reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, force, cfg->nq, cfg->ng, cfg->box, s);
 }
 
@@ -170,7 +195,7 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
     if (!state_ok(st, true) || step < 0 || step >= cfg->n_steps) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
-    if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s))) return rc;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
     return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st,
                                     table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
                                     step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
@@ -271,6 +296,54 @@ int cola_fft3d_c2r(int32_t n, float* data, void* ws, size_t ws_bytes, void* stre
     if ((rc = fft_strided(c, n, 0, +1, tw, s))) return rc;
     if ((rc = fft_strided(c, n, 1, +1, tw, s))) return rc;
     return fft_z_c2r(c, n, tw, s, nullptr, 0, 1.f, fft_pitch(n), (long long)n * n);
+}
+
+int cola_net_pack(const cola_net* net, void* stream) { return net_pack(net, S(stream)); }
+
+int cola_net_grad(const cola_config* cfg, const cola_state* st, double a, const float* target, float* grad,
+                  double* loss, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!(cfg->flags & COLA_FLAG_LEARNED) || !state_ok(st, false) || !target || !grad || !loss || !(a > 0.0))
+        return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    const double green = 1.5 * cfg->cosmo.omega_m / a;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
+    return net_backward(cfg->net, wsp(ws, L.lrn), cfg->ng, cfg->nq, cfg->box, (float)green,
+                        reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, target, grad, loss, s);
+}
+
+int cola_adam(float* params, const float* grad, float* m, float* v, int32_t n, int32_t t, float lr, float beta1,
+              float beta2, float eps, void* stream) {
+    if (!params || !grad || !m || !v || n <= 0 || t < 1) return COLA_EINVAL;
+    return launch_adam(params, grad, m, v, n, t, lr, beta1, beta2, eps, S(stream));
+}
+
+int cola_filter_accumulate(const cola_config* cfg, const cola_state* st, double a, const float* target, int32_t nb,
+                           float* basis, double* ATA, double* ATy, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, false) || !target || !basis || !ATA || !ATy || nb < 2 || nb > 64 || !(a > 0.0))
+        return COLA_EINVAL;
+    cudaStream_t s = S(stream);
+    const double green = 1.5 * cfg->cosmo.omega_m / a;
+    const long long np3 = 3ll * cfg->nq * cfg->nq * cfg->nq;
+    float* table = reinterpret_cast<float*>(wsp(ws, kHdrFilter));
+    for (int b = 0; b < nb; ++b) {
+        if ((rc = launch_basis_table(table, nb, b, s))) return rc;
+        if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s, table, nb, false))) return rc;
+        if ((rc = launch_gather(reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, basis + (size_t)b * np3, cfg->nq,
+                                cfg->ng, cfg->box, s)))
+            return rc;
+    }
+    return launch_lsq_accumulate(basis, target, np3, nb, ATA, ATy, s);
+}
+
+int cola_filter_solve(const double* ATA, const double* ATy, int32_t nb, double ridge, float* T, void* stream) {
+    if (!ATA || !ATy || !T || nb < 2 || nb > 64 || !(ridge >= 0.0)) return COLA_EINVAL;
+    return launch_lsq_solve(ATA, ATy, nb, ridge, T, S(stream));
 }
 
 int cola_status(void* ws, size_t ws_bytes, void* stream) {

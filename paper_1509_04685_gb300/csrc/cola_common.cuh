@@ -393,6 +393,7 @@ constexpr size_t kHdrStatus = 0;          // int: latched device status
 constexpr size_t kHdrSigmaAmp = 64;       // double: P(k) amplitude A (sigma8 normalisation)
 constexpr size_t kHdrSnap = 128;          // 3 doubles: snapshot drift coefficients (dr, dD1, dD2)
 constexpr size_t kHdrGrowthScratch = 256; // small FP64 scratch for the snapshot growth call
+constexpr size_t kHdrFilter = 1024;       // radial filter basis table (<= 64 floats)
 constexpr size_t kHdrTable = 4096;        // kMaxSteps x kTableCols doubles
 constexpr size_t kHdrTwiddle = 262144;    // 3 slots of kMaxFft float2
 constexpr size_t kHdrBytes = 524288;
@@ -404,6 +405,7 @@ struct Layout {
     size_t F;          // interleaved force mesh: ng x ng x 3 rows of P complex (delta_k in component 0)
     size_t ic;         // 2LPT scratch: 7 complex meshes of nq x nq x Pq (aliases dep..)
     size_t pk_part;    // P(k) per-block partial sums (after the first two thirds of F)
+    size_t lrn;        // learned-correction buffers (COLA_FLAG_LEARNED), 0 otherwise
     size_t total;
 };
 
@@ -452,7 +454,7 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // ---------------------------------------------------------------------------
 enum KernelId {
     kKDeposit = 0, kKZr2cFix, kKZr2c, kKYFwd, kKXFwd, kKXGreen, kKYInv, kKXInv, kKZc2r, kKGatherKD, kKGather,
-    kKFixToDelta, kKPkShells, kKPkReduce, kKIc, kKSetup, kNumKernelIds
+    kKFixToDelta, kKPkShells, kKPkReduce, kKIc, kKSetup, kKLearned, kNumKernelIds
 };
 class ProfScope {
   public:
@@ -483,7 +485,9 @@ int fft_lines(float2* data, int n, int sign, const float2* tw, cudaStream_t s, L
 // plain n x n x P mesh, axis 1 = y, 0 = x
 int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaStream_t s);
 // interleaved force mesh (rows (ix, iy, c)): delta_k in c = 0 -> F_x, F_y, F_z in c = 0, 1, 2
-int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s);
+// filt: optional radial transfer function T(|k|) on nodes b * fstep, b < nfilt (nullptr: none)
+int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s,
+                const float* filt = nullptr, int nfilt = 0, float fstep = 1.f);
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
                       int nq, int ng, double box, const double* snap, int* status, cudaStream_t s);
@@ -491,7 +495,10 @@ int launch_deposit_ex(const float* d, const float* v, const float* psi1, const f
 int launch_gather(const float2* F, const float* d, float* out, int nq, int ng, double box, cudaStream_t s);
 int launch_gather_kick_drift(const float2* F, cola_state st, const double* row, int nq, int ng, double box, int last,
                              int pm_only, int* status, cudaStream_t s);
-int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s);
+int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s,
+                        bool clear = true);
+int launch_adjoint_deposit(const float* d, const float* res, unsigned long long* fix3, int nq, int ng, double box,
+                           cudaStream_t s);
 
 int launch_tables(const cola_config* cfg, double* table, cudaStream_t s);
 int launch_snapshot_coeffs(const cola_config* cfg, double a_node, double a_out, double* snap, cudaStream_t s);
@@ -499,5 +506,18 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
 int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
                  double* nmodes, int nbins, cudaStream_t s);
 size_t power_partial_bytes(int nbins);
+
+// learned coarse-mesh correction (learned.cu)
+size_t learned_bytes(int ng, int nq);
+int net_pack(const cola_net* net, cudaStream_t s);
+int net_forward(const cola_net* net, char* lbase, int ng, int nq, float green, float2* F, cudaStream_t s);
+int net_backward(const cola_net* net, char* lbase, int ng, int nq, double box, float green, const float2* F,
+                 const float* d, const float* target, float* grad, double* loss, cudaStream_t s);
+int launch_adam(float* p, const float* g, float* m, float* v, int n, int t, float lr, float b1, float b2, float eps,
+                cudaStream_t s);
+int launch_lsq_accumulate(const float* A, const float* y, long long len, int nb, double* ATA, double* ATy,
+                          cudaStream_t s);
+int launch_lsq_solve(const double* ATA, const double* ATy, int nb, double ridge, float* T, cudaStream_t s);
+int launch_basis_table(float* T, int nb, int b, cudaStream_t s);
 
 }  // namespace cola

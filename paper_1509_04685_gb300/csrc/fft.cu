@@ -330,7 +330,8 @@ constexpr int kGreenEpt = 12;  // spectrum values each thread keeps in registers
 
 __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f0, float2* f1, float2* f2,
                                                      int n, long long RS, int B, int nct, int ntiles, FftPlan plan,
-                                                     const float2* __restrict__ tw, float gscale, float kf) {
+                                                     const float2* __restrict__ tw, float gscale, float kf,
+                                                     const float* __restrict__ filt, int nfilt, float fstep) {
     extern __shared__ float2 sm[];
     const int tsz = spad(n) * B;
     float2* stg = sm;
@@ -372,7 +373,16 @@ __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f
                 const float kx = kf * (float)(i < half ? i : i - n);
                 const float kz = kf * (float)(col0 + c);
                 const float k2 = kx * kx + ky * ky + kz * kz;
-                phi[q] = cscale(X[c + spad(i) * B], k2 > 0.f ? gscale / k2 : 0.f);
+                float gk = k2 > 0.f ? gscale / k2 : 0.f;
+                if (filt) {
+                    // learned radial transfer T(|k|), piecewise linear on nodes b * fstep
+                    const float u = sqrtf(k2) / fstep;
+                    int b = (int)u;
+                    if (b > nfilt - 2) b = nfilt - 2;
+                    const float f = fminf(u - (float)b, 1.f);
+                    gk *= (1.f - f) * filt[b] + f * filt[b + 1];
+                }
+                phi[q] = cscale(X[c + spad(i) * B], gk);
             }
         }
         __syncthreads();
@@ -514,7 +524,8 @@ int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaS
                      axis == 1 ? (sign < 0 ? kKYFwd : kKYInv) : (sign < 0 ? kKXFwd : kKXInv));
 }
 
-int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s) {
+int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s, const float* filt,
+                int nfilt, float fstep) {
     FftPlan plan;
     if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
     const long long P = fft_pitch(n);
@@ -530,7 +541,7 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     ProfScope ps(kKXGreen, s);
     // interleaved force mesh: rows (ix, iy, c) of P complex, delta_k in c = 0
     k_fft_x_green<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, F, F + P, F + 2 * P, n, 3 * P, B, nct, ntiles,
-                                                                  plan, tw, gscale, kf);
+                                                                  plan, tw, gscale, kf, filt, nfilt, fstep);
     return check_launch();
 }
 

@@ -216,17 +216,62 @@ int launch_gather_kick_drift(const float2* Fm, cola_state st, const double* row,
 // --------------------------------------------------------------------------
 // fixed-point mesh -> delta (unpadded float ng^3); clears the fixed-point mesh
 // --------------------------------------------------------------------------
-__global__ void k_fix_to_delta(unsigned long long* dep, float* delta, long long n3, float scale) {
+__global__ void k_fix_to_delta(unsigned long long* dep, float* delta, long long n3, float scale, int clear) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n3) return;
     delta[i] = (float)dep[i] * scale - 1.0f;
-    dep[i] = 0ull;
+    if (clear) dep[i] = 0ull;
 }
 
-int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s) {
+int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float scale, cudaStream_t s, bool clear) {
     const long long n3 = (long long)ng * ng * ng;
     ProfScope ps(kKFixToDelta, s);
-    k_fix_to_delta<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(dep, delta, n3, scale);
+    k_fix_to_delta<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(dep, delta, n3, scale, clear ? 1 : 0);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// adjoint of the CIC gather: deposit per-particle vectors res (SoA 3 x Np)
+// with the gather's weights into three signed fixed-point meshes (2^30 per
+// unit, two's complement in uint64 atomics: order-independent)
+// --------------------------------------------------------------------------
+__global__ void k_adjoint_deposit(const float* __restrict__ d, const float* __restrict__ res,
+                                  unsigned long long* __restrict__ fix3, int nq, int ng, float inv_cell, long long np) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float dx[3] = {d[p], d[np + p], d[2 * np + p]};
+    Cic c;
+    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) return;
+    const long long n3 = (long long)ng * ng * ng;
+    const float wx[2] = {1.f - c.f[0], c.f[0]};
+    const float wy[2] = {1.f - c.f[1], c.f[1]};
+    const float wz[2] = {1.f - c.f[2], c.f[2]};
+    const int ix[2] = {c.c0[0], c.c1[0]};
+    const int iy[2] = {c.c0[1], c.c1[1]};
+    const int iz[2] = {c.c0[2], c.c1[2]};
+    const float r[3] = {res[p], res[np + p], res[2 * np + p]};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float w = wx[a] * wy[b] * wz[e];
+                const long long cell = ((long long)ix[a] * ng + iy[b]) * ng + iz[e];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const long long q = __float2ll_rn(w * r[j] * 1073741824.0f);  // 2^30
+                    atomicAdd(fix3 + j * n3 + cell, (unsigned long long)q);
+                }
+            }
+}
+
+int launch_adjoint_deposit(const float* d, const float* res, unsigned long long* fix3, int nq, int ng, double box,
+                           cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    ProfScope ps(kKDeposit, s);
+    k_adjoint_deposit<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(d, res, fix3, nq, ng, (float)((double)ng / box),
+                                                                   np);
     return check_launch();
 }
 
