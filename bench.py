@@ -35,7 +35,81 @@ WORKLOADS = {
     "full": dict(name="cola_512^3_particles_1536^3_mesh_L1536_40steps", nq=512, ng=1536, box=1536.0),
     "mid": dict(name="cola_256^3_particles_768^3_mesh_L768_40steps", nq=256, ng=768, box=768.0),
     "small": dict(name="cola_32^3_particles_96^3_mesh_L128_40steps", nq=32, ng=96, box=128.0),
+    # 48 seeds: 16 each at 96^3, 128^3, 160^3 particles, PM_grid cycling 1, 2, 3, L = 1 Mpc/h per spacing
+    "ensemble": dict(name="cola_ensemble_48_seeds_96-128-160^3_pm1-2-3_40steps", nq=0, ng=0, box=0.0),
 }
+
+
+def ensemble_members():
+    out = []
+    for i in range(48):
+        nq = (96, 128, 160)[i // 16]
+        m = 1 + i % 3
+        out.append((nq, m * nq, float(nq), 1 + i))
+    return out
+
+
+def run_ensemble(args, rank, world, C, torch, dist):
+    """One timed step = one graph launch replaying the 2LPT set-up and all 40
+    nodes of this rank's members (members i = rank mod world)."""
+    mem = [m for i, m in enumerate(ensemble_members()) if i % world == rank]
+    cfgs = [C.make_config(nq, ng, box, A_INIT, 1.0, N_NODES) for nq, ng, box, _ in mem]
+    sims = [C.Simulation(c) for c in cfgs]
+    # autotune the tile width of every mesh size once
+    scratch_n = max(c.ng for c in cfgs)
+    scratch = torch.zeros(scratch_n * scratch_n * 2 * C.cola_fft_pitch(scratch_n), dtype=torch.float32,
+                          device="cuda")
+    tuned = {}
+    for c, sm in zip(cfgs, sims):
+        for n in (c.ng, c.nq):
+            if n not in tuned:
+                tuned[n] = C.cola_fft_autotune(n, scratch, sm.ws)
+    del scratch
+    # one uncaptured step per member sets kernel attributes before capture
+    for c, sm, (_, _, _, seed) in zip(cfgs, sims, mem):
+        sm.ic(seed)
+        sm.step(0)
+    ens = C.Ensemble(cfgs, [m[3] for m in mem], [sm.state for sm in sims], [sm.ws for sm in sims], nstreams=8)
+    for _ in range(max(1, args.warmup // 3)):
+        ens.launch()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    launches0 = C.cola_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrep = max(1, args.steps // 12)
+    e0.record()
+    for _ in range(nrep):
+        ens.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    for sm in sims:
+        if sm.status() != 0:
+            raise SystemExit("device status after ensemble")
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ps_local = sum(nq**3 for nq, _, _, _ in mem) * N_NODES
+    ps = torch.tensor([float(ps_local)], device="cuda")
+    if dist:
+        dist.all_reduce(ps)
+    value = float(ps.item()) * nrep / (ms * 1e-3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "particle-steps/s (48-seed uneven ensemble, one CUDA-graph launch per run)", "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": nrep, "warmup": max(1, args.warmup // 3),
+            "ms_per_step": ms / nrep, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["ensemble"]["name"], "members": 48, "n_steps": N_NODES,
+                       "step": "one graph launch = 2LPT set-up + 40 nodes of every member",
+                       "autotuned_tiles": {str(k): v for k, v in sorted(tuned.items())},
+                       "parallelism": f"members sharded over {world} rank(s)"},
+            "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
+        }), flush=True)
 A_INIT, N_NODES = 0.05, 40
 METRIC = "particle-steps/s at 512^3/1536^3"
 UNIT = "particle-steps/s"
@@ -226,6 +300,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    if args.workload == "ensemble":
+        run_ensemble(args, rank, world, C, torch, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     w = WORKLOADS[args.workload]
     cfg = C.make_config(w["nq"], w["ng"], w["box"], A_INIT, 1.0, N_NODES)
     sim = C.Simulation(cfg, device=f"cuda:{local}")

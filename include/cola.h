@@ -217,6 +217,27 @@ int cola_filter_solve(const double* ATA, const double* ATy, int32_t nb, double r
  * it first.  Non-finite particle data turns the whole output into NaN. */
 int cola_density_noalloc(const cola_config* cfg, const cola_state* st, float* delta, void* stream);
 
+/* Ensembles of independent realisations (Sec. 6 uses 48 realisations to beat
+ * down sampling variance).  cola_ensemble_create captures, once, every
+ * member's work (2LPT set-up when step_from == 0, then nodes
+ * step_from .. step_to-1) into one CUDA graph: members are spread over
+ * nstreams concurrent streams, largest first onto the least loaded stream.
+ * cfgs, seeds, states, ws, ws_bytes are arrays of n (host arrays of device
+ * pointers); sizes may differ between members.  cola_ensemble_launch replays
+ * the whole ensemble with one graph launch on `stream`. */
+typedef struct cola_ensemble cola_ensemble;
+int cola_ensemble_create(int32_t n, const cola_config* cfgs, const uint64_t* seeds, const cola_state* states,
+                         void* const* ws, const size_t* ws_bytes, int32_t nstreams, int32_t step_from,
+                         int32_t step_to, cola_ensemble** out);
+int cola_ensemble_launch(cola_ensemble* e, void* stream);
+void cola_ensemble_destroy(cola_ensemble* e);
+
+/* FFT tile autotuner: times the y pass of an n^3 mesh (device buffer of
+ * n*n*2*cola_fft_pitch(n) floats, contents destroyed) for each admissible
+ * column width and keeps the fastest for all later passes of that size in this
+ * process; *best receives it (may be NULL). */
+int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* stream, int32_t* best);
+
 /* Per-kernel timing (tracing): between cola_profile_start and
  * cola_profile_stop every kernel launch of the library is bracketed by CUDA
  * events on its own stream (at most max_records launches are recorded).

@@ -84,6 +84,10 @@ def _load():
                       ctypes.c_int),
         "cola_filter_accumulate": ([cfgp, stp, dbl, vp, i32, vp, vp, vp, vp, sz, vp], ctypes.c_int),
         "cola_filter_solve": ([vp, vp, i32, dbl, vp, vp], ctypes.c_int),
+        "cola_ensemble_create": ([i32, cfgp, vp, stp, vp, vp, i32, i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "cola_ensemble_launch": ([vp, vp], ctypes.c_int),
+        "cola_ensemble_destroy": ([vp], None),
+        "cola_fft_autotune": ([i32, vp, vp, sz, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "cola_profile_start": ([i32], ctypes.c_int),
         "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
         "cola_num_kernel_ids": ([], i32),
@@ -161,6 +165,40 @@ def cola_filter_accumulate(cfg, st: cola_state, a: float, target, nb: int, basis
 
 def cola_filter_solve(ATA, ATy, nb: int, ridge: float, T, stream=None):
     _check(LIB.cola_filter_solve(_ptr(ATA), _ptr(ATy), nb, ridge, _ptr(T), _stream(stream)), "cola_filter_solve")
+
+
+class Ensemble:
+    """One CUDA graph replaying the 2LPT set-up and nodes [step_from, step_to)
+    of every member (cola_ensemble_create); members are (cfg, seed, state, ws)."""
+
+    def __init__(self, cfgs, seeds, states, workspaces, nstreams=8, step_from=0, step_to=None):
+        n = len(cfgs)
+        self._cfgs = (cola_config * n)(*cfgs)
+        self._seeds = (ctypes.c_uint64 * n)(*seeds)
+        self._states = (cola_state * n)(*states)
+        self._ws = (ctypes.c_void_p * n)(*[_ptr(w) for w in workspaces])
+        self._wsb = (ctypes.c_size_t * n)(*[w.numel() * w.element_size() for w in workspaces])
+        self._keep = (cfgs, states, workspaces)
+        st_to = cfgs[0].n_steps if step_to is None else step_to
+        h = ctypes.c_void_p()
+        _check(LIB.cola_ensemble_create(n, self._cfgs, self._seeds, self._states, self._ws, self._wsb, nstreams,
+                                        step_from, st_to, ctypes.byref(h)), "cola_ensemble_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(LIB.cola_ensemble_launch(self.handle, _stream(stream)), "cola_ensemble_launch")
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            LIB.cola_ensemble_destroy(self.handle)
+            self.handle = None
+
+
+def cola_fft_autotune(n: int, mesh, ws, stream=None) -> int:
+    best = ctypes.c_int32(0)
+    _check(LIB.cola_fft_autotune(n, _ptr(mesh), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
+                                 ctypes.byref(best)), "cola_fft_autotune")
+    return best.value
 
 
 def make_state(d, v=None, psi1=None, psi2=None) -> cola_state:

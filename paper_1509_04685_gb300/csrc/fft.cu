@@ -422,9 +422,26 @@ static int z_rows_per_block(int M) {
     return nr;
 }
 
+// Raise a kernel's dynamic shared-memory limit once per size (also keeps the
+// attribute call out of stream captures after the first, uncaptured use).
 static bool set_smem(const void* fn, size_t bytes) {
     if (bytes <= 48 * 1024) return true;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+    static const void* fns[64];
+    static size_t done[64];
+    static int nf = 0;
+    for (int i = 0; i < nf; ++i)
+        if (fns[i] == fn && done[i] >= bytes) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+    for (int i = 0; i < nf; ++i)
+        if (fns[i] == fn) {
+            done[i] = bytes;
+            return true;
+        }
+    if (nf < 64) {
+        fns[nf] = fn;
+        done[nf++] = bytes;
+    }
+    return true;
 }
 
 // threads: about one butterfly of the first (largest-radix) pass per thread
@@ -478,8 +495,13 @@ int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out,
     return check_launch();
 }
 
-// adjacent kz columns per block: two ping-pong buffers of n*B complex each
-static int strided_cols(int n) { return n <= 256 ? 16 : (n <= 768 ? 8 : (n <= 2048 ? 4 : 2)); }
+// adjacent kz columns per block: the autotuned width if cola_fft_autotune ran
+// for this size, else a default that keeps the three tile buffers near 100 KB
+extern int g_tile_choice[kMaxFft + 1];
+static int strided_cols(int n) {
+    if (n <= kMaxFft && g_tile_choice[n]) return g_tile_choice[n];
+    return n <= 256 ? 16 : (n <= 768 ? 8 : (n <= 2048 ? 4 : 2));
+}
 
 static int g_num_sms = 0;
 static int num_sms() {
