@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "full": dict(name="cola_512^3_particles_1536^3_mesh_L1536_40steps", nq=512, ng=1536, box=1536.0),
     "mid": dict(name="cola_256^3_particles_768^3_mesh_L768_40steps", nq=256, ng=768, box=768.0),
+    "largest": dict(name="cola_768^3_particles_2304^3_mesh_L1536_40steps", nq=768, ng=2304, box=1536.0),
     "small": dict(name="cola_32^3_particles_96^3_mesh_L128_40steps", nq=32, ng=96, box=128.0),
     # 48 seeds: 16 each at 96^3, 128^3, 160^3 particles, PM_grid cycling 1, 2, 3, L = 1 Mpc/h per spacing
     "ensemble": dict(name="cola_ensemble_48_seeds_96-128-160^3_pm1-2-3_40steps", nq=0, ng=0, box=0.0),
@@ -112,6 +113,8 @@ def run_ensemble(args, rank, world, C, torch, dist):
         }), flush=True)
 A_INIT, N_NODES = 0.05, 40
 METRIC = "particle-steps/s at 512^3/1536^3"
+METRICS = {"largest": "particle-steps/s at 768^3/2304^3", "mid": "particle-steps/s at 256^3/768^3",
+           "small": "particle-steps/s at 32^3/96^3"}
 UNIT = "particle-steps/s"
 FALLBACK_HBM = 6800.0
 
@@ -388,7 +391,8 @@ def main():
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRICS.get(args.workload, METRIC), "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "nq": w["nq"], "ng": w["ng"], "box": w["box"], "n_steps": N_NODES,

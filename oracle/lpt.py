@@ -29,6 +29,24 @@ import numpy as np
 
 from .philox import white_noise_grid
 
+# FFT backend: numpy.fft (pocketfft), or scipy.fft's pocketfft with worker
+# threads when FFT_WORKERS > 1 (same algorithm; used for full-size references)
+FFT_WORKERS = 1
+
+
+def _rfftn(x):
+    if FFT_WORKERS > 1:
+        import scipy.fft
+        return scipy.fft.rfftn(x, workers=FFT_WORKERS)
+    return np.fft.rfftn(x)
+
+
+def _irfftn(x, shape):
+    if FFT_WORKERS > 1:
+        import scipy.fft
+        return scipy.fft.irfftn(x, s=shape, axes=(0, 1, 2), workers=FFT_WORKERS)
+    return np.fft.irfftn(x, s=shape, axes=(0, 1, 2))
+
 
 def kgrid(n: int, L: float):
     """Signed wavenumbers (kx, ky) on the full axes and kz on the half axis,
@@ -51,7 +69,7 @@ def linear_delta_k(noise: np.ndarray, L: float, pk) -> np.ndarray:
     kx, ky, kz, nx, ny, nz = kgrid(n, L)
     k = np.sqrt(kx**2 + ky**2 + kz**2)
     dq3 = (L / n) ** 3
-    wk = np.fft.rfftn(noise)
+    wk = _rfftn(noise)
     dk = wk * np.sqrt(pk(k) / dq3)
     dk = np.where(nx | ny | nz, 0.0, dk)
     dk[0, 0, 0] = 0.0
@@ -67,18 +85,18 @@ def lpt_from_delta_k(dk: np.ndarray, L: float):
     k2 = kx**2 + ky**2 + kz**2
     k2[0, 0, 0] = 1.0
     shape = (n, n, n)
-    psi1 = np.stack([np.fft.irfftn(1j * kv[i] * dk / k2, s=shape, axes=(0, 1, 2)) for i in range(3)])
+    psi1 = np.stack([_irfftn(1j * kv[i] * dk / k2, shape) for i in range(3)])
     # phi1_ij = IFFT[ -k_i k_j phi1_k ] = IFFT[ k_i k_j delta_k / k^2 ]
     phi = {}
     for i in range(3):
         for j in range(i, 3):
-            phi[i, j] = np.fft.irfftn(kv[i] * kv[j] * dk / k2, s=shape, axes=(0, 1, 2))
+            phi[i, j] = _irfftn(kv[i] * kv[j] * dk / k2, shape)
     delta2 = (phi[0, 0] * phi[1, 1] + phi[0, 0] * phi[2, 2] + phi[1, 1] * phi[2, 2]
               - phi[0, 1] ** 2 - phi[0, 2] ** 2 - phi[1, 2] ** 2)
-    d2k = np.fft.rfftn(delta2)
+    d2k = _rfftn(delta2)
     d2k = np.where(nx | ny | nz, 0.0, d2k)
     d2k[0, 0, 0] = 0.0
-    psi2 = np.stack([np.fft.irfftn(-1j * kv[i] * d2k / k2, s=shape, axes=(0, 1, 2)) for i in range(3)])
+    psi2 = np.stack([_irfftn(-1j * kv[i] * d2k / k2, shape) for i in range(3)])
     return psi1, psi2, delta2
 
 

@@ -17,6 +17,8 @@ def test_numpy_fft_matches_direct_dft(shape):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
     back = np.real(dft.dftn(dft.dftn(x), +1)) / x.size
     np.testing.assert_allclose(back, x, atol=1e-12)
+    import scipy.fft  # the threaded backend of oracle.lpt for full-size references
+    assert np.abs(scipy.fft.rfftn(x, workers=2) - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_direct_dft_single_mode():
