@@ -105,13 +105,18 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     // the net's input keeps delta in real space (first buffer of the learned region)
     if (learned && (rc = launch_fix_to_delta(dep, reinterpret_cast<float*>(wsp(ws, L.lrn)), ng, scale, s, false)))
         return rc;
-    if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, 3 * P, n2))) return rc;
-    if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * P, ng, 1, ng * 3 * P, 0}, kKYFwd))) return rc;
+    const FRow fr = force_rows(ng);
+    const long long XB = 1ll << fr.xbs;
+    if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, P, n2, fr))) return rc;
+    // y lines of component 0 (outer x = xb XB + xi), then of all three components (outer 3 x + c)
+    if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * XB * P, ng, (int)XB, 3 * XB * ng * P, 3 * P}, kKYFwd)))
+        return rc;
     const double kmax = std::sqrt(3.0) * 3.14159265358979323846 * ng / cfg->box;
     if ((rc = fft_x_green(F, ng, (float)(green / ng3), (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s, filt,
                           nfilt, nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f)))
         return rc;
-    if ((rc = fft_lines(F, ng, +1, tw, s, LineGeom{3 * P, 3 * ng, 3, ng * 3 * P, P}, kKYInv))) return rc;
+    if ((rc = fft_lines(F, ng, +1, tw, s, LineGeom{3 * XB * P, 3 * ng, (int)(3 * XB), 3 * XB * ng * P, P}, kKYInv)))
+        return rc;
     if ((rc = fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2))) return rc;
     if (learned) return net_forward(cfg->net, wsp(ws, L.lrn), ng, nq, (float)green, F, s);
     return COLA_OK;
@@ -230,7 +235,7 @@ int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t no
         return rc;
     const long long Ppk = fft_pitch(ng_pk);
     if ((rc = fft_z_r2c(dep, mk, ng_pk, (float)(ratio * ratio * ratio / 1099511627776.0), tw, s, Ppk,
-                        (long long)ng_pk * ng_pk)))
+                        (long long)ng_pk * ng_pk, FRow{ng_pk, 0, 1})))
         return rc;
     if ((rc = fft_strided(mk, ng_pk, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(mk, ng_pk, 0, -1, tw, s))) return rc;
@@ -281,7 +286,7 @@ int cola_fft3d_r2c(int32_t n, float* data, void* ws, size_t ws_bytes, void* stre
     const float2* tw = twiddles_for(n, nullptr, ws, s, &rc);
     if (rc) return rc;
     float2* c = reinterpret_cast<float2*>(data);
-    if ((rc = fft_z_r2c(nullptr, c, n, 0.f, tw, s, fft_pitch(n), (long long)n * n))) return rc;
+    if ((rc = fft_z_r2c(nullptr, c, n, 0.f, tw, s, fft_pitch(n), (long long)n * n, FRow{n, 0, 1}))) return rc;
     if ((rc = fft_strided(c, n, 1, -1, tw, s))) return rc;
     return fft_strided(c, n, 0, -1, tw, s);
 }

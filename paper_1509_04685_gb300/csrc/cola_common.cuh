@@ -298,6 +298,20 @@ __device__ __forceinline__ void fft_pass_any(int R, const In& in, const Out& out
     }
 }
 
+// Force-mesh row of (x, y, component c): x is blocked by XB = 2^xbs so that a
+// line along x (stride n XB comps P between blocks) touches n / XB memory
+// pages instead of n, while a line along y spans XB times more; rows
+// ((x / XB) n + y) XB + x mod XB, each holding `comps` component rows.
+struct FRow {
+    int n, xbs, comps;
+};
+__host__ __device__ __forceinline__ long long frow(int x, int y, int c, const FRow& f) {
+    return ((((long long)(x >> f.xbs) * f.n + y) << f.xbs) + (x & ((1 << f.xbs) - 1))) * f.comps + c;
+}
+__host__ __device__ __forceinline__ int xblock_shift(int n) {
+    return n % 8 == 0 ? 3 : (n % 4 == 0 ? 2 : (n % 2 == 0 ? 1 : 0));
+}
+
 struct LineGeom {
     long long S;   // element stride along the transformed axis
     int nouter;    // number of outer indices
@@ -476,8 +490,9 @@ inline int check_launch() {
 
 int launch_twiddles(float2* tw, int n, cudaStream_t s);
 // z passes: row r at base + r*rs (complex units), nrows rows
+// r2c: input row r = x n + y goes to output row frow(x, y, 0, fr) (fr = {n, 0, 1}: in place, same row)
 int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,
-              long long rs, long long nrows);
+              long long rs, long long nrows, FRow fr);
 int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out, long long opitch, float oscale,
               long long rs, long long nrows);
 // line passes: tile of outer index o starts at (o / o2n) s1 + (o % o2n) s2, element stride S
@@ -488,6 +503,7 @@ int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaS
 // filt: optional radial transfer function T(|k|) on nodes b * fstep, b < nfilt (nullptr: none)
 int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s,
                 const float* filt = nullptr, int nfilt = 0, float fstep = 1.f);
+__host__ __device__ __forceinline__ FRow force_rows(int ng) { return FRow{ng, xblock_shift(ng), 3}; }
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
                       int nq, int ng, double box, const double* snap, int* status, cudaStream_t s);

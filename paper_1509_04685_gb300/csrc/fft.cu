@@ -205,10 +205,35 @@ struct ColIO {
 // Psi = IFFT_x(phi) stored twice: F_y = i k_y Psi and F_z = i k_z Psi.  Along
 // an x line k_y (fixed row iy) and k_z (fixed column) are constants, so they
 // commute with the inverse x transform: one transform serves both components.
+// x-line addressing of the blocked force mesh: element i at
+// (i >> xbs) Sb + (i & (XB - 1)) Si
+struct XLine {
+    long long Sb, Si;
+    int xbs;
+    __device__ __forceinline__ long long off(int i) const {
+        return (long long)(i >> xbs) * Sb + (long long)(i & ((1 << xbs) - 1)) * Si;
+    }
+};
+
+struct XIO {
+    float2* g;
+    XLine xl;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcs(g + xl.off(i0 + r * di) + l);
+    }
+    template <int R>
+    __device__ __forceinline__ void store(int l, int i0, int di, const float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(g + xl.off(i0 + r * di) + l, v[r]);
+    }
+};
+
 struct YZStore {
     float2* fy;
     float2* fz;
-    long long S;
+    XLine xl;
     float ky;             // 0 on the y Nyquist plane
     float kf;
     int col0, half;
@@ -217,7 +242,7 @@ struct YZStore {
         const float kz = (col0 + l == half) ? 0.f : kf * (float)(col0 + l);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const long long q = (long long)(i0 + r * di) * S + l;
+            const long long q = xl.off(i0 + r * di) + l;
             __stcs(fy + q, make_float2(-ky * v[r].y, ky * v[r].x));
             __stcs(fz + q, make_float2(-kz * v[r].y, kz * v[r].x));
         }
@@ -233,12 +258,18 @@ struct YZStore {
 // ---------------------------------------------------------------------------
 template <bool FIX>
 __global__ void k_fft_z_r2c(unsigned long long* __restrict__ dep, float2* out, int n, long long rs, long long nrows,
-                            int NR, float scale, FftPlan plan, const float2* __restrict__ tw, FastDiv m1div) {
+                            int NR, float scale, FftPlan plan, const float2* __restrict__ tw, FastDiv m1div, FRow fr) {
     extern __shared__ float2 sm[];
+    __shared__ long long obase[64];  // output row offsets of this block's lines
     const int M = n / 2;
     const int ls = spad(M) + 1;
     float2* sb = sm + NR * ls;
     const long long row0 = (long long)blockIdx.x * NR;
+    if (threadIdx.x < NR) {
+        const long long r = row0 + threadIdx.x;
+        const int x = (int)(r / n), y = (int)(r - (long long)x * n);
+        obase[threadIdx.x] = frow(x, y, 0, fr) * rs;
+    }
     const FftGeom g{NR, ls, 1, false, 0, 2};
     const float2* Z;
     if (FIX)
@@ -254,7 +285,7 @@ __global__ void k_fft_z_r2c(unsigned long long* __restrict__ dep, float2* out, i
         const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
         const float2 D = csub(a, b);
         const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // (a-b)/(2i)
-        out[row * rs + k] = cadd(E, cmul(__ldg(&tw[k]), O));
+        out[obase[l] + k] = cadd(E, cmul(__ldg(&tw[k]), O));
     }
 }
 
@@ -329,9 +360,10 @@ __global__ void k_fft_strided(float2* data, int n, LineGeom lg, int B, int nct, 
 constexpr int kGreenEpt = 12;  // spectrum values each thread keeps in registers
 
 __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f0, float2* f1, float2* f2,
-                                                     int n, long long RS, int B, int nct, int ntiles, FftPlan plan,
-                                                     const float2* __restrict__ tw, float gscale, float kf,
-                                                     const float* __restrict__ filt, int nfilt, float fstep) {
+                                                     int n, long long RS, XLine xl, int B, int nct, int ntiles,
+                                                     FftPlan plan, const float2* __restrict__ tw, float gscale,
+                                                     float kf, const float* __restrict__ filt, int nfilt,
+                                                     float fstep) {
     extern __shared__ float2 sm[];
     const int tsz = spad(n) * B;
     float2* stg = sm;
@@ -339,18 +371,27 @@ __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f
     float2* W = A + tsz;
     float2* tws = W + tsz;  // twiddle table, copied once per persistent block
     for (int q = threadIdx.x; q < n; q += blockDim.x) tws[q] = __ldg(tw + q);
-    const long long S = (long long)n * RS;  // x stride; RS = stride of the y index
     const int T = blockDim.x;
     const int bs = __ffs(B) - 1;
     const int half = n / 2;
     const FftGeom g{B, 1, B, true, bs, 1};
+    // RS: offset of one y row (the x lines of the tile start at iy RS)
     auto tile_off = [&](int t) {
         const int iy = t / nct;
         const int ct = t - iy * nct;
         return (long long)iy * RS + ct * B;
     };
+    auto prefetch = [&](const float2* g0) {
+        const int hb = B >> 1;
+        const int hs = __ffs(hb) - 1;
+        for (int e = threadIdx.x; e < n * hb; e += blockDim.x) {
+            const int i = e >> hs, c = (e & (hb - 1)) << 1;
+            cp_async16(stg + c + spad(i) * B, g0 + xl.off(i) + c);
+        }
+        cp_async_commit();
+    };
     int t = blockIdx.x;
-    if (t < ntiles) tile_prefetch(stg, mk + tile_off(t), n, B, S);
+    if (t < ntiles) prefetch(mk + tile_off(t));
     for (; t < ntiles; t += gridDim.x) {
         const int iy = t / nct;
         const int col0 = (t - iy * nct) * B;
@@ -359,7 +400,7 @@ __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f
         __syncthreads();
         const int tn = t + gridDim.x;
         auto prefetch_next = [&]() {
-            if (tn < ntiles) tile_prefetch(stg, mk + tile_off(tn), n, B, S);
+            if (tn < ntiles) prefetch(mk + tile_off(tn));
         };
         const float2* X = fft_run_smem<-1, true>(SmemIO{stg, 1, B}, A, W, plan, g, tws, prefetch_next);
         const float ky = kf * (float)(iy < half ? iy : iy - n);
@@ -404,10 +445,10 @@ __global__ void __launch_bounds__(512) k_fft_x_green(const float2* mk, float2* f
             }
             __syncthreads();
             if (j == 0)
-                fft_run_out<+1, true>(SmemIO{A, 1, B}, ColIO{f0 + off, S}, W, A, plan, g, tws);
+                fft_run_out<+1, true>(SmemIO{A, 1, B}, XIO{f0 + off, xl}, W, A, plan, g, tws);
             else
-                fft_run_out<+1, true>(SmemIO{A, 1, B}, YZStore{f1 + off, f2 + off, S, ky_eff, kf, col0, half}, W, A,
-                                      plan, g, tws);
+                fft_run_out<+1, true>(SmemIO{A, 1, B}, YZStore{f1 + off, f2 + off, xl, ky_eff, kf, col0, half}, W,
+                                      A, plan, g, tws);
         }
     }
 }
@@ -454,7 +495,7 @@ static int pass_threads(const FftPlan& plan, long lines) {
 }
 
 int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,
-              long long rs, long long nrows) {
+              long long rs, long long nrows, FRow fr) {
     FftPlan plan;
     if (!make_plan(n / 2, &plan)) return COLA_EUNSUPPORTED_SIZE;
     const int M = n / 2;
@@ -466,11 +507,11 @@ int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const fl
     if (dep) {
         if (!set_smem((const void*)k_fft_z_r2c<true>, smem)) return COLA_ECUDA;
         k_fft_z_r2c<true><<<(unsigned)grid, T, smem, s>>>(dep, out, n, rs, nrows, NR, scale, plan, tw,
-                                                           make_fastdiv(M + 1));
+                                                           make_fastdiv(M + 1), fr);
     } else {
         if (!set_smem((const void*)k_fft_z_r2c<false>, smem)) return COLA_ECUDA;
         k_fft_z_r2c<false><<<(unsigned)grid, T, smem, s>>>(nullptr, out, n, rs, nrows, NR, 0.f, plan, tw,
-                                                            make_fastdiv(M + 1));
+                                                            make_fastdiv(M + 1), fr);
     }
     return check_launch();
 }
@@ -561,9 +602,12 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
     if (!set_smem((const void*)k_fft_x_green, smem)) return COLA_ECUDA;
     ProfScope ps(kKXGreen, s);
-    // interleaved force mesh: rows (ix, iy, c) of P complex, delta_k in c = 0
-    k_fft_x_green<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, F, F + P, F + 2 * P, n, 3 * P, B, nct, ntiles,
-                                                                  plan, tw, gscale, kf, filt, nfilt, fstep);
+    // interleaved, x-blocked force mesh: rows frow(x, y, c) of P complex, delta_k in c = 0
+    const FRow fr = force_rows(n);
+    const int XB = 1 << fr.xbs;
+    const XLine xl{3ll * XB * n * P, 3 * P, fr.xbs};
+    k_fft_x_green<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, F, F + P, F + 2 * P, n, 3ll * XB * P, xl, B, nct,
+                                                                  ntiles, plan, tw, gscale, kf, filt, nfilt, fstep);
     return check_launch();
 }
 

@@ -392,7 +392,7 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
     }
     if ((rc = check_launch())) return rc;
     const long long nrows = (long long)nq * nq;
-    if ((rc = fft_z_r2c(nullptr, b[0], nq, 0.f, tw, s, P, nrows))) return rc;
+    if ((rc = fft_z_r2c(nullptr, b[0], nq, 0.f, tw, s, P, nrows, FRow{nq, 0, 1}))) return rc;
     if ((rc = fft_strided(b[0], nq, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(b[0], nq, 0, -1, tw, s))) return rc;
     {
@@ -434,7 +434,7 @@ int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, co
                                        (const float*)b[5], (const float*)b[6], nq, 2ll * P);
     }
     if ((rc = check_launch())) return rc;
-    if ((rc = fft_z_r2c(nullptr, b[1], nq, 0.f, tw, s, P, nrows))) return rc;
+    if ((rc = fft_z_r2c(nullptr, b[1], nq, 0.f, tw, s, P, nrows, FRow{nq, 0, 1}))) return rc;
     if ((rc = fft_strided(b[1], nq, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(b[1], nq, 0, -1, tw, s))) return rc;
     for (int a = 0; a < 3; ++a) {

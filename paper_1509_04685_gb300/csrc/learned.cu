@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kConvWarps * 32) k_conv(const bf16* __restrict
                     r1 = __bfloat162float(m.y) > 0.f ? r1 : 0.f;
                     *reinterpret_cast<__nv_bfloat162*>(out + v * COUT + co) = __floats2bfloat162_rn(r0, r1);
                 } else {
-                    const long long row = ((long long)vx * N + vy) * 3;
+                    const FRow fr = force_rows(N);
+                    const long long row = frow(vx, vy, 0, fr);
                     if (co < 3) F[(row + co) * P2 + vz] += scale * (r0 + bias[co]);
                     if (co + 1 < 3) F[(row + co + 1) * P2 + vz] += scale * (r1 + bias[co + 1]);
                 }
@@ -255,9 +256,12 @@ __global__ void k_pack_input(const float* __restrict__ delta, const float* __res
     if (v >= n3) return;
     const long long row = v / N;
     const int z = (int)(v - row * N);
+    const int ix = (int)(row / N), iy = (int)(row - (long long)ix * N);
+    const FRow fr = force_rows(N);
+    const long long fb = frow(ix, iy, 0, fr) * P2 + z;
     float c[16];
     c[0] = delta[v];
-    for (int j = 0; j < 3; ++j) c[1 + j] = F[(row * 3 + j) * P2 + z] * inv_g;
+    for (int j = 0; j < 3; ++j) c[1 + j] = F[fb + j * P2] * inv_g;
     for (int j = 4; j < 16; ++j) c[j] = 0.f;
     uint4* o = reinterpret_cast<uint4*>(x + v * 16);
     for (int q = 0; q < 2; ++q) {

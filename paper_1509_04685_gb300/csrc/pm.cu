@@ -113,12 +113,14 @@ int launch_deposit_ex(const float* d, const float* v, const float* psi1, const f
 }
 
 // --------------------------------------------------------------------------
-// CIC interpolation of the three force components from the interleaved force
-// mesh (real view): component j of cell (ix, iy, z) at ((ix ng + iy) 3 + j) P2 + z,
-// P2 = 2P floats, so the three components of a cell are P2 apart.
+// CIC interpolation of the three force components from the interleaved,
+// x-blocked force mesh (real view): component j of cell (ix, iy, z) at
+// frow(ix, iy, j) P2 + z, P2 = 2P floats, so the three components of a cell
+// are P2 apart.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ void gather3(const float* __restrict__ Fm, int ng, long long P2, const Cic& c,
                                         float F[3]) {
+    const FRow fr = force_rows(ng);
     F[0] = F[1] = F[2] = 0.f;
     const int ix[2] = {c.c0[0], c.c1[0]};
     const int iy[2] = {c.c0[1], c.c1[1]};
@@ -130,7 +132,7 @@ __device__ __forceinline__ void gather3(const float* __restrict__ Fm, int ng, lo
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const long long row = ((long long)ix[a] * ng + iy[b]) * 3 * P2;
+            const long long row = frow(ix[a], iy[b], 0, fr) * P2;
             const float wab = wx[a] * wy[b];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
