@@ -88,6 +88,7 @@ def _load():
         "cola_ensemble_launch": ([vp, vp], ctypes.c_int),
         "cola_ensemble_destroy": ([vp], None),
         "cola_fft_autotune": ([i32, vp, vp, sz, vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "cola_fft_set_tile": ([i32, i32], ctypes.c_int),
         "cola_profile_start": ([i32], ctypes.c_int),
         "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
         "cola_num_kernel_ids": ([], i32),
@@ -199,6 +200,10 @@ def cola_fft_autotune(n: int, mesh, ws, stream=None) -> int:
     _check(LIB.cola_fft_autotune(n, _ptr(mesh), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream),
                                  ctypes.byref(best)), "cola_fft_autotune")
     return best.value
+
+
+def cola_fft_set_tile(n: int, B: int) -> None:
+    _check(LIB.cola_fft_set_tile(n, B), "cola_fft_set_tile")
 
 
 def make_state(d, v=None, psi1=None, psi2=None) -> cola_state:

@@ -212,8 +212,50 @@ struct FftPlan {
     FastDiv nbl_div[kMaxRadices];  // division by n / radix[s]
 };
 
-// Factor n into radices 8, 4, 2, 3, 5 (largest powers of two first).
-// Returns false if n has another prime factor or is out of range.
+// Radix list of a length-n transform: threes are paired with spare factors of
+// two (12 = 4*3, 6 = 2*3), the remaining twos go in 16s, then 8/4/2, then the
+// leftover 3s and 5s; sorted largest first (the first pass reads global memory
+// and needs no twiddles).  ok = false if n has another prime factor.
+struct StaticPlan {
+    bool ok;
+    int nr;
+    int r[kMaxRadices];
+};
+__host__ __device__ constexpr StaticPlan static_plan(int n) {
+    StaticPlan p{false, 0, {}};
+    if (n < 1 || n > kMaxFft) return p;
+    int m = n, a = 0, b = 0, c = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    while (m % 5 == 0) { m /= 5; ++c; }
+    if (m != 1) return p;
+    int nr = 0;
+    const int pairs = b < a / 2 ? b : a / 2;
+    for (int i = 0; i < pairs; ++i) p.r[nr++] = 12;
+    a -= 2 * pairs;
+    b -= pairs;
+    if (b > 0 && a > 0) { p.r[nr++] = 6; --a; --b; }
+    while (a >= 4) { p.r[nr++] = 16; a -= 4; }
+    if (a == 3) p.r[nr++] = 8;
+    if (a == 2) p.r[nr++] = 4;
+    if (a == 1) p.r[nr++] = 2;
+    while (b-- > 0) p.r[nr++] = 3;
+    while (c-- > 0) p.r[nr++] = 5;
+    for (int i = 0; i < nr; ++i)
+        for (int j = i + 1; j < nr; ++j)
+            if (p.r[j] > p.r[i]) { const int t = p.r[i]; p.r[i] = p.r[j]; p.r[j] = t; }
+    p.nr = nr;
+    p.ok = true;
+    return p;
+}
+// product of the radices before pass s
+__host__ __device__ constexpr int plan_ls(const StaticPlan& p, int s) {
+    int ls = 1;
+    for (int i = 0; i < s; ++i) ls *= p.r[i];
+    return ls;
+}
+
+// Runtime plan of static_plan(n).  Returns false if n is unsupported.
 bool make_plan(int n, FftPlan* p);
 
 // ---------------------------------------------------------------------------
@@ -231,7 +273,7 @@ bool make_plan(int n, FftPlan* p);
 // ---------------------------------------------------------------------------
 // Shared-memory element i of a line sits at i + i/16: one pad slot per 16
 // elements keeps the stride-R accesses of a Stockham pass off a single bank.
-__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int spad(int i) { return i + (i >> 4); }
 
 struct SmemIO {
     float2* p;
@@ -308,7 +350,7 @@ struct FRow {
 __host__ __device__ __forceinline__ long long frow(int x, int y, int c, const FRow& f) {
     return ((((long long)(x >> f.xbs) * f.n + y) << f.xbs) + (x & ((1 << f.xbs) - 1))) * f.comps + c;
 }
-__host__ __device__ __forceinline__ int xblock_shift(int n) {
+__host__ __device__ constexpr int xblock_shift(int n) {
     return n % 8 == 0 ? 3 : (n % 4 == 0 ? 2 : (n % 2 == 0 ? 1 : 0));
 }
 
@@ -423,10 +465,7 @@ struct Layout {
     size_t total;
 };
 
-inline int fft_pitch(int n) {
-    int h = n / 2 + 1;
-    return (h + 15) / 16 * 16;
-}
+__host__ __device__ constexpr int fft_pitch(int n) { return (n / 2 + 1 + 15) / 16 * 16; }
 inline size_t mesh_bytes(int n) { return (size_t)n * n * fft_pitch(n) * 8; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool layout_for(const cola_config* cfg, Layout* L);
@@ -489,6 +528,10 @@ inline int check_launch() {
 }
 
 int launch_twiddles(float2* tw, int n, cudaStream_t s);
+// raise a kernel's dynamic shared-memory limit (cached per kernel and size)
+bool set_smem(const void* fn, size_t bytes);
+// persistent grid: blocks per SM from the shared-memory budget, at most ntiles
+int persistent_grid(size_t smem, int ntiles);
 // z passes: row r at base + r*rs (complex units), nrows rows
 // r2c: input row r = x n + y goes to output row frow(x, y, 0, fr) (fr = {n, 0, 1}: in place, same row)
 int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,

@@ -137,6 +137,14 @@ void cola_ensemble_destroy(cola_ensemble* e) {
     delete e;
 }
 
+int cola_fft_set_tile(int32_t n, int32_t B) {
+    if (n < 2 || n > kMaxFft) return COLA_EINVAL;
+    if (B != 0 && B != 2 && B != 4 && B != 8 && B != 16) return COLA_EINVAL;
+    if (B && (size_t)(3 * spad(n) * B + n) * 8 > 220 * 1024) return COLA_EINVAL;
+    g_tile_choice[n] = B;
+    return COLA_OK;
+}
+
 // Time the y pass of an n^3 mesh for every admissible column width and keep
 // the fastest for this n (used by every later strided pass of that size).
 int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* stream, int32_t* best) {

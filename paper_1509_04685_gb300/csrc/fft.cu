@@ -8,46 +8,21 @@
 // Forward passes run z (r2c), y, x; inverse passes x, y, z (c2r).
 #include <cmath>
 
-#include "cola_common.cuh"
+#include "fft_static.cuh"
 
 namespace cola {
 
 unsigned long long g_launches = 0;
 
-// Radices 16, 12, 8, 6, 5, 4, 3, 2: threes are paired with spare factors of
-// two (12 = 4*3, 6 = 2*3), the remaining twos go in 16s, then 8/4/2.
 bool make_plan(int n, FftPlan* p) {
-    if (n < 1 || n > kMaxFft) return false;
-    int m = n, a = 0, b = 0, c = 0;
-    while (m % 2 == 0) { m /= 2; ++a; }
-    while (m % 3 == 0) { m /= 3; ++b; }
-    while (m % 5 == 0) { m /= 5; ++c; }
-    if (m != 1) return false;
-    int list[kMaxRadices], nr = 0;
-    auto push = [&](int r) { if (nr < kMaxRadices) list[nr++] = r; };
-    int pairs = b < a / 2 ? b : a / 2;
-    for (int i = 0; i < pairs; ++i) push(12);
-    a -= 2 * pairs;
-    b -= pairs;
-    if (b > 0 && a > 0) { push(6); --a; --b; }
-    while (a >= 4) { push(16); a -= 4; }
-    if (a == 3) push(8);
-    if (a == 2) push(4);
-    if (a == 1) push(2);
-    while (b-- > 0) push(3);
-    while (c-- > 0) push(5);
-    // largest radix first (the first pass reads global memory and needs no twiddles)
-    for (int i = 0; i < nr; ++i)
-        for (int j = i + 1; j < nr; ++j)
-            if (list[j] > list[i]) { int t = list[i]; list[i] = list[j]; list[j] = t; }
+    const StaticPlan sp = static_plan(n);
+    if (!sp.ok) return false;
     p->n = n;
-    p->nr = nr;
-    int Ls = 1;
-    for (int s = 0; s < nr; ++s) {
-        p->radix[s] = list[s];
-        p->ls_div[s] = make_fastdiv(Ls);
-        p->nbl_div[s] = make_fastdiv(n / list[s]);
-        Ls *= list[s];
+    p->nr = sp.nr;
+    for (int s = 0; s < sp.nr; ++s) {
+        p->radix[s] = sp.r[s];
+        p->ls_div[s] = make_fastdiv(plan_ls(sp, s));
+        p->nbl_div[s] = make_fastdiv(n / sp.r[s]);
     }
     return true;
 }
@@ -465,7 +440,7 @@ static int z_rows_per_block(int M) {
 
 // Raise a kernel's dynamic shared-memory limit once per size (also keeps the
 // attribute call out of stream captures after the first, uncaptured use).
-static bool set_smem(const void* fn, size_t bytes) {
+bool set_smem(const void* fn, size_t bytes) {
     if (bytes <= 48 * 1024) return true;
     static const void* fns[64];
     static size_t done[64];
@@ -556,7 +531,7 @@ static int num_sms() {
 
 // Persistent blocks: three tile buffers (prefetch + ping-pong), blocks per SM
 // from the shared-memory budget.
-static int persistent_grid(size_t smem, int ntiles) {
+int persistent_grid(size_t smem, int ntiles) {
     int per_sm = (int)((227 * 1024) / (smem + 1024));
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms() * per_sm;
@@ -571,11 +546,13 @@ int fft_lines(float2* data, int n, int sign, const float2* tw, cudaStream_t s, L
     const long long ntl = (long long)lg.nouter * nct;
     if (ntl > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
     const int ntiles = (int)ntl;
+    ProfScope ps(kid, s);
+    int rc = COLA_OK;
+    if (launch_strided_static(data, n, B, sign, lg, nct, ntiles, tw, s, &rc)) return rc;
     int T = pass_threads(plan, B) * 2;
     const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
     auto kern = sign < 0 ? k_fft_strided<-1> : k_fft_strided<+1>;
     if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
-    ProfScope ps(kid, s);
     kern<<<persistent_grid(smem, ntiles), T, smem, s>>>(data, n, lg, B, nct, ntiles, plan, tw);
     return check_launch();
 }
@@ -596,12 +573,14 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     while (B > 2 && n * B > 512 * kGreenEpt) B /= 2;
     const int nct = (n / 2 + 1 + B - 1) / B;
     const int ntiles = n * nct;
+    ProfScope ps(kKXGreen, s);
+    int rc = COLA_OK;
+    if (launch_x_green_static(F, n, B, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s, &rc)) return rc;
     int T = ((n * B + kGreenEpt - 1) / kGreenEpt + 31) / 32 * 32;
     if (T < 64) T = 64;
     if (T > 512) return COLA_EUNSUPPORTED_SIZE;
     const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
     if (!set_smem((const void*)k_fft_x_green, smem)) return COLA_ECUDA;
-    ProfScope ps(kKXGreen, s);
     // interleaved, x-blocked force mesh: rows frow(x, y, c) of P complex, delta_k in c = 0
     const FRow fr = force_rows(n);
     const int XB = 1 << fr.xbs;

@@ -44,8 +44,7 @@ def plin():
 
 
 # ---------------------------------------------------------------- FFT ------
-@pytest.mark.parametrize("n", [4, 6, 8, 10, 12, 18, 20, 30, 48, 96, 160, 250, 384])
-def test_fft3d_r2c_c2r_vs_numpy(n):
+def _check_fft3d(n):
     x = random_mesh(n, (n, n, n)).astype(np.float64)
     P = C.cola_fft_pitch(n)
     buf = torch.zeros((n, n, 2 * P), dtype=torch.float32, device="cuda")
@@ -59,6 +58,32 @@ def test_fft3d_r2c_c2r_vs_numpy(n):
     C.cola_fft3d_c2r(n, buf, ws)
     back = host(buf)[:, :, :n] / n**3
     assert rel_l2(back, f32(x)) < 1e-6
+
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12, 18, 20, 30, 48, 96, 128, 160, 192, 250, 256, 384])
+def test_fft3d_r2c_c2r_vs_numpy(n):
+    _check_fft3d(n)
+
+
+# (n, B): every specialised strided-pass tile (compile-time n and width) and
+# runtime-engine widths next to them; cola_fft_set_tile forces the width
+TILE_CASES = [(96, 16), (128, 16), (160, 16), (192, 16), (256, 8), (256, 16), (288, 16), (288, 8), (320, 16),
+              (320, 4), (384, 8), (384, 16), (480, 8), (480, 16), (250, 2)]
+
+
+@pytest.mark.parametrize("n,B", TILE_CASES)
+def test_fft3d_tile_widths_vs_numpy(n, B):
+    C.cola_fft_set_tile(n, B)
+    try:
+        _check_fft3d(n)
+    finally:
+        C.cola_fft_set_tile(n, 0)
+
+
+def test_fft_set_tile_rejects_bad_widths():
+    for n, B in ((96, 3), (96, 32), (1, 4), (8192, 4), (4096, 16)):
+        with pytest.raises(C.ColaError):
+            C.cola_fft_set_tile(n, B)
 
 
 def test_fft_rejects_bad_sizes():
@@ -116,6 +141,29 @@ def test_pm_force_vs_oracle_initial_field(nq, ng, L, plin, growth):
     sim.d.copy_(dev(d))
     got = host(sim.force(0.05))
     ref = pm.pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / 0.05)
+    assert rel_l2(got, ref) < 1e-5
+
+
+# (nq, ng, B): the fused Green pass and the y passes at every specialised
+# tile, on seeded Gaussian displacements of 0.7 particle spacings rms
+FORCE_TILE_CASES = [(48, 96, 16), (64, 128, 16), (80, 160, 16), (64, 192, 16), (128, 256, 8), (128, 256, 16),
+                    (96, 288, 16), (160, 320, 16), (128, 384, 8), (128, 384, 16), (160, 480, 8), (160, 480, 16),
+                    (64, 192, 4)]
+
+
+@pytest.mark.parametrize("nq,ng,B", FORCE_TILE_CASES)
+def test_pm_force_tile_widths_vs_oracle(nq, ng, B):
+    L = float(ng)
+    d = f32(random_displacements(11, nq, 0.7 * L / nq))
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    C.cola_fft_set_tile(ng, B)
+    try:
+        got = host(sim.force(0.5))
+    finally:
+        C.cola_fft_set_tile(ng, 0)
+    ref = pm.pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / 0.5)
     assert rel_l2(got, ref) < 1e-5
 
 
