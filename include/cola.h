@@ -240,10 +240,9 @@ int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* s
 
 /* Set the column width B (2, 4, 8 or 16 adjacent columns per tile) of every
  * later strided pass of line length n in this process, as the autotuner does;
- * B = 0 restores the built-in default.  The fused Green pass halves B while
- * n * B > 6144.  Results do not depend on B (same arithmetic per line).
- * Returns COLA_EINVAL for n outside 2..4096, another B, or a B whose three
- * tile buffers exceed the shared memory of one block. */
+ * B = 0 restores the built-in default.  Results do not depend on B (same
+ * arithmetic per line).  Returns COLA_EINVAL for n outside 2..4096, another B,
+ * or a B whose tile buffers exceed the shared memory of one block. */
 int cola_fft_set_tile(int32_t n, int32_t B);
 
 /* Per-kernel timing (tracing): between cola_profile_start and

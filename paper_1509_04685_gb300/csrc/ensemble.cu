@@ -12,7 +12,7 @@
 #include <cmath>
 #include <vector>
 
-#include "cola_common.cuh"
+#include "fft_static.cuh"
 
 struct cola_ensemble {
     cudaGraph_t graph = nullptr;
@@ -140,7 +140,7 @@ void cola_ensemble_destroy(cola_ensemble* e) {
 int cola_fft_set_tile(int32_t n, int32_t B) {
     if (n < 2 || n > kMaxFft) return COLA_EINVAL;
     if (B != 0 && B != 2 && B != 4 && B != 8 && B != 16) return COLA_EINVAL;
-    if (B && (size_t)(3 * spad(n) * B + n) * 8 > 220 * 1024) return COLA_EINVAL;
+    if (B && !static_tile_ok(n, B) && (size_t)(3 * spad(n) * B + n) * 8 > 220 * 1024) return COLA_EINVAL;
     g_tile_choice[n] = B;
     return COLA_OK;
 }
@@ -158,8 +158,9 @@ int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* s
     float best_ms = 1e30f;
     int best_b = 0;
     for (int B : {2, 4, 8, 16}) {
-        // three ping-pong/prefetch buffers of n*B complex must fit in shared memory
-        if ((size_t)(3 * spad(n) * B + n) * 8 > 220 * 1024) continue;
+        // the specialised passes (two tile buffers) or the runtime ones (three)
+        // must fit in shared memory
+        if (!static_tile_ok(n, B) && (size_t)(3 * spad(n) * B + n) * 8 > 220 * 1024) continue;
         g_tile_choice[n] = B;
         float ms = 0.f;
         for (int rep = 0; rep < 3 && !rc; ++rep) {

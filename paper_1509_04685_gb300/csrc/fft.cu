@@ -479,6 +479,8 @@ int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const fl
     const size_t smem = (size_t)2 * NR * (spad(M) + 1) * 8;
     const long long grid = (nrows + NR - 1) / NR;
     ProfScope ps(dep ? kKZr2cFix : kKZr2c, s);
+    int rc = COLA_OK;
+    if (dep && launch_z_r2c_fix_static(dep, out, n, rs, nrows, scale, tw, fr, s, &rc)) return rc;
     if (dep) {
         if (!set_smem((const void*)k_fft_z_r2c<true>, smem)) return COLA_ECUDA;
         k_fft_z_r2c<true><<<(unsigned)grid, T, smem, s>>>(dep, out, n, rs, nrows, NR, scale, plan, tw,
@@ -501,6 +503,8 @@ int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out,
     const size_t smem = (size_t)2 * NR * (spad(M) + 1) * 8;
     const long long grid = (nrows + NR - 1) / NR;
     ProfScope ps(kKZc2r, s);
+    int rc = COLA_OK;
+    if (!out && launch_z_c2r_static(data, n, rs, nrows, tw, s, &rc)) return rc;
     if (out) {
         if (!set_smem((const void*)k_fft_z_c2r<true>, smem)) return COLA_ECUDA;
         k_fft_z_c2r<true><<<(unsigned)grid, T, smem, s>>>(data, n, rs, nrows, NR, plan, tw, out, opitch, oscale);
@@ -516,8 +520,12 @@ int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out,
 extern int g_tile_choice[kMaxFft + 1];
 static int strided_cols(int n) {
     if (n <= kMaxFft && g_tile_choice[n]) return g_tile_choice[n];
+    if (const int b = static_tile(n)) return b;
     return n <= 256 ? 16 : (n <= 768 ? 8 : (n <= 2048 ? 4 : 2));
 }
+
+// a column width the runtime engine (three tile buffers) can run
+static bool runtime_tile_fits(int n, int B) { return (size_t)(3 * spad(n) * B + n) * 8 <= 220 * 1024; }
 
 static int g_num_sms = 0;
 static int num_sms() {
@@ -549,6 +557,7 @@ int fft_lines(float2* data, int n, int sign, const float2* tw, cudaStream_t s, L
     ProfScope ps(kid, s);
     int rc = COLA_OK;
     if (launch_strided_static(data, n, B, sign, lg, nct, ntiles, tw, s, &rc)) return rc;
+    if (!runtime_tile_fits(n, B)) return COLA_EUNSUPPORTED_SIZE;
     int T = pass_threads(plan, B) * 2;
     const size_t smem = ((size_t)3 * spad(n) * B + n) * 8;
     auto kern = sign < 0 ? k_fft_strided<-1> : k_fft_strided<+1>;
@@ -569,13 +578,17 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     FftPlan plan;
     if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
     const long long P = fft_pitch(n);
-    int B = strided_cols(n);
-    while (B > 2 && n * B > 512 * kGreenEpt) B /= 2;
-    const int nct = (n / 2 + 1 + B - 1) / B;
-    const int ntiles = n * nct;
+    const int bg = static_green_tile(n);
+    int B = (n <= kMaxFft && g_tile_choice[n]) || !bg ? strided_cols(n) : bg;
     ProfScope ps(kKXGreen, s);
     int rc = COLA_OK;
-    if (launch_x_green_static(F, n, B, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s, &rc)) return rc;
+    {
+        const int nct = (n / 2 + 1 + B - 1) / B;
+        if (launch_x_green_static(F, n, B, nct, n * nct, tw, gscale, kf, filt, nfilt, fstep, s, &rc)) return rc;
+    }
+    while (B > 2 && (n * B > 512 * kGreenEpt || !runtime_tile_fits(n, B))) B /= 2;
+    const int nct = (n / 2 + 1 + B - 1) / B;
+    const int ntiles = n * nct;
     int T = ((n * B + kGreenEpt - 1) / kGreenEpt + 31) / 32 * 32;
     if (T < 64) T = 64;
     if (T > 512) return COLA_EUNSUPPORTED_SIZE;

@@ -1,23 +1,28 @@
 // Specialised strided and fused x/Green passes (fft_static.cuh) for the large
-// meshes: 768^3, 1152^3, 1536^3 and 2304^3.
+// meshes: 768^3, 1152^3, 1536^3 and 2304^3, the tile-width tables and the
+// specialised z passes.
 #include "fft_static.cuh"
 
 namespace cola {
 
-// (n, B, threads) of every specialisation; B is a tile width the runtime
-// engine or the tile autotuner picks for n, so a specialisation replaces
-// exactly the runtime kernel's launch for that (n, B)
+// (n, B, threads) of every specialisation: B adjacent columns per tile, two
+// tile buffers of spad(n) B complex in shared memory
 #define COLA_STRIDED_SPECS(X) \
+    X(768, 16, 1024) \
     X(768, 8, 512) \
-    X(1152, 4, 512) \
-    X(1536, 4, 512) \
-    X(2304, 2, 512)
+    X(1152, 8, 1024) \
+    X(1536, 8, 1024) \
+    X(2304, 4, 1024)
 
 #define COLA_XGREEN_SPECS(X) \
-    X(768, 8, 512) \
-    X(1152, 4, 384) \
-    X(1536, 4, 512) \
-    X(2304, 2, 384)
+    X(768, 16, 768, 2)       \
+    X(768, 8, 1024, 3)       \
+    X(1152, 8, 768, 2)       \
+    X(1152, 4, 768, 3)       \
+    X(1536, 8, 768, 2)       \
+    X(1536, 4, 1024, 3)      \
+    X(2304, 4, 768, 2)       \
+    X(2304, 2, 768, 3)
 
 bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, int nct, int ntiles,
                            const float2* tw, cudaStream_t s, int* rc) {
@@ -33,14 +38,74 @@ bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, in
 
 bool launch_x_green_static(float2* F, int n, int B, int nct, int ntiles, const float2* tw, float gscale,
                            float kf, const float* filt, int nfilt, float fstep, cudaStream_t s, int* rc) {
-#define COLA_CASE(NN, BB, TT)                                                                  \
-    if (n == NN && B == BB) {                                                                  \
-        *rc = run_x_green<NN, BB, TT>(F, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s); \
-        return true;                                                                           \
+#define COLA_CASE(NN, BB, TT, NBUF)                                                                  \
+    if (n == NN && B == BB) {                                                                        \
+        *rc = run_x_green<NN, BB, TT, NBUF>(F, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s); \
+        return true;                                                                                 \
     }
     COLA_XGREEN_SPECS(COLA_CASE)
 #undef COLA_CASE
     return launch_x_green_static_small(F, n, B, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s, rc);
 }
+
+// default column width of the specialised line passes of each size
+static const int kStaticTiles[][2] = {{96, 16}, {128, 16}, {160, 16}, {192, 16}, {256, 16}, {288, 16}, {320, 16}, {384, 16}, {480, 16}, {768, 16}, {1152, 8}, {1536, 8}, {2304, 4}};
+static const int kStaticSpecs[][2] = {{96, 16}, {128, 16}, {160, 16}, {192, 16}, {256, 16}, {256, 8}, {288, 16}, {320, 16}, {384, 16}, {384, 8}, {480, 16}, {480, 8}, {768, 16}, {768, 8}, {1152, 8}, {1536, 8}, {2304, 4}};
+
+// default column width of the specialised fused x/Green pass of each size
+static const int kGreenTiles[][2] = {{768, 8}, {1152, 4}, {1536, 8}, {2304, 2}};
+
+int static_green_tile(int n) {
+    for (const auto& e : kGreenTiles)
+        if (e[0] == n) return e[1];
+    return launch_static_green_tile_small(n);
+}
+
+int static_tile(int n) {
+    for (const auto& e : kStaticTiles)
+        if (e[0] == n) return e[1];
+    return 0;
+}
+
+bool static_tile_ok(int n, int B) {
+    for (const auto& e : kStaticSpecs)
+        if (e[0] == n && e[1] == B) return true;
+    return false;
+}
+
+// (n, rows per tile, threads, blocks per SM of the c2r and the r2c kernel) of
+// the z-pass specialisations
+#define COLA_Z_SPECS(X)        \
+    X(256, 16, 256, 1, 1)      \
+    X(384, 8, 128, 1, 1)       \
+    X(768, 8, 256, 2, 2)       \
+    X(1152, 4, 256, 2, 2)      \
+    X(1536, 4, 256, 2, 2)      \
+    X(2304, 2, 256, 2, 2)
+
+bool launch_z_c2r_static(float2* data, int n, long long rs, long long nrows, const float2* tw, cudaStream_t s,
+                         int* rc) {
+#define COLA_CASE(NN, RR, TT, MC, MR)                        \
+    if (n == NN) {                                           \
+        *rc = run_z_c2r<NN, RR, TT, MC>(data, rs, nrows, tw, s); \
+        return true;                                         \
+    }
+    COLA_Z_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return false;
+}
+
+bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long long rs, long long nrows,
+                             float scale, const float2* tw, FRow fr, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, RR, TT, MC, MR)                                               \
+    if (n == NN) {                                                                  \
+        *rc = run_z_r2c_fix<NN, RR, TT, MR>(dep, out, rs, nrows, scale, tw, fr, s); \
+        return true;                                                                \
+    }
+    COLA_Z_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return false;
+}
+
 
 }  // namespace cola

@@ -13,19 +13,37 @@
 
 namespace cola {
 
-// padded line-interleaved tile in shared memory: element i of line l at l + spad(i) B
+// Shape of a tile in shared memory: NL lines, element (l, i) at
+// l LSTR + spad(i) ES; LF: butterflies run over the lines first (consecutive
+// threads take adjacent lines; NL a power of two), else along a line.  TWM is
+// the twiddle table's stride: the table holds N TWM entries exp(-2 pi i q / (N TWM)).
+template <int NL_, bool LF_, int LSTR_, int ES_, int TWM_>
+struct TileGeo {
+    static constexpr int NL = NL_;
+    static constexpr bool LF = LF_;
+    static constexpr int LSTR = LSTR_;
+    static constexpr int ES = ES_;
+    static constexpr int TWM = TWM_;
+};
+// B interleaved columns (strided y/x passes)
 template <int B>
+using ColTile = TileGeo<B, true, 1, B, 1>;
+// NR rows of the half-length complex transform of real rows of 2M values (z passes)
+template <int M, int NR>
+using RowTile = TileGeo<NR, false, spad(M) + 1, 1, 2>;
+
+template <class Geo>
 struct SSmem {
     float2* p;
     template <int R, int D>
     __device__ __forceinline__ void load(int l, int i0, float2* v) const {
         if constexpr (D % 16 == 0) {
-            const float2* q = p + l + spad(i0) * B;
+            const float2* q = p + l * Geo::LSTR + spad(i0) * Geo::ES;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = q[r * spad(D) * B];
+            for (int r = 0; r < R; ++r) v[r] = q[r * spad(D) * Geo::ES];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = p[l + spad(i0 + r * D) * B];
+            for (int r = 0; r < R; ++r) v[r] = p[l * Geo::LSTR + spad(i0 + r * D) * Geo::ES];
         }
     }
     // stores come from butterflies with i0 = jq LS R + k: for LS = D = 1 the
@@ -34,41 +52,46 @@ struct SSmem {
     template <int R, int D>
     __device__ __forceinline__ void store(int l, int i0, const float2* v) const {
         if constexpr (D % 16 == 0 || (D == 1 && 16 % R == 0)) {
-            float2* q = p + l + spad(i0) * B;
+            float2* q = p + l * Geo::LSTR + spad(i0) * Geo::ES;
 #pragma unroll
-            for (int r = 0; r < R; ++r) q[r * spad(D) * B] = v[r];
+            for (int r = 0; r < R; ++r) q[r * spad(D) * Geo::ES] = v[r];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) p[l + spad(i0 + r * D) * B] = v[r];
+            for (int r = 0; r < R; ++r) p[l * Geo::LSTR + spad(i0 + r * D) * Geo::ES] = v[r];
         }
     }
 };
 
-// One Stockham pass of radix R over a tile of B lines (see fft_pass for the
-// index map): butterfly b = (j, l), j < N / R, k = j mod LS,
+// One Stockham pass of radix R over a tile of Geo::NL lines of length N (see
+// fft_pass for the index map): butterfly b = (j, l), j < N / R, k = j mod LS,
 //   v_r = in(l, j + r N/R) W_{LS R}^{r k},  v = DFT_R(v),  out(l, (j / LS) LS R + k + r LS) = v_r.
-template <int N, int B, int T, int R, int LS, int SIGN, class In, class Out>
+template <int N, int T, class Geo, int R, int LS, int SIGN, class In, class Out>
 __device__ __forceinline__ void spass(const In& in, const Out& out, const float2* __restrict__ tw) {
     constexpr int NBL = N / R;
-    constexpr int NB = NBL * B;
+    constexpr int NB = NBL * Geo::NL;
     constexpr int IT = (NB + T - 1) / T;
-    constexpr int TWS = N / (LS * R);
+    constexpr int TWS = N / (LS * R) * Geo::TWM;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const unsigned b = threadIdx.x + (unsigned)(it * T);
         if (NB % T != 0 && it == IT - 1 && b >= (unsigned)NB) break;
-        const int l = (int)(b % B);
-        const int j = (int)(b / B);
+        int l, j;
+        if constexpr (Geo::LF) {
+            l = (int)(b % Geo::NL);
+            j = (int)(b / Geo::NL);
+        } else {
+            l = (int)(b / NBL);
+            j = (int)(b - (unsigned)l * NBL);
+        }
         const int jq = (int)((unsigned)j / LS);
         const int k = j - jq * LS;
         float2 v[R];
         in.template load<R, NBL>(l, j, v);
         if constexpr (LS > 1) {
-            const float2* tq = tw;
             const int step = k * TWS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tq[r * step];
+                float2 w = tw[r * step];
                 if (SIGN > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -79,43 +102,143 @@ __device__ __forceinline__ void spass(const In& in, const Out& out, const float2
 }
 
 // passes S .. nr-1: S reads a; the last pass writes `out`
-template <int N, int B, int T, int SIGN, int S, class Out>
+template <int N, int T, class Geo, int SIGN, int S, class Out>
 __device__ __forceinline__ void srun_tail(float2* a, float2* b, const Out& out, const float2* __restrict__ tw) {
     constexpr StaticPlan P = static_plan(N);
     constexpr int R = P.r[S];
     constexpr int LS = plan_ls(P, S);
     if constexpr (S == P.nr - 1) {
-        spass<N, B, T, R, LS, SIGN>(SSmem<B>{a}, out, tw);
+        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
         __syncthreads();
     } else {
-        spass<N, B, T, R, LS, SIGN>(SSmem<B>{a}, SSmem<B>{b}, tw);
+        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{b}, tw);
         __syncthreads();
-        srun_tail<N, B, T, SIGN, S + 1>(b, a, out, tw);
+        srun_tail<N, T, Geo, SIGN, S + 1>(b, a, out, tw);
     }
 }
 
 // Transform reading `in` in the first pass (into a), then `hook` (uniform:
 // the input is no longer needed), the middle passes ping-pong a/b, the last
 // pass writes `out`.  Needs at least two passes.  Returns synchronised.
-template <int N, int B, int T, int SIGN, class In, class Out, class Hook>
+template <int N, int T, class Geo, int SIGN, class In, class Out, class Hook>
 __device__ __forceinline__ void srun_out(const In& in, const Out& out, float2* a, float2* b,
                                          const float2* __restrict__ tw, const Hook& hook) {
     constexpr StaticPlan P = static_plan(N);
     static_assert(P.ok && P.nr >= 2, "specialised transforms need two or more passes");
-    spass<N, B, T, P.r[0], 1, SIGN>(in, SSmem<B>{a}, tw);
+    spass<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
     __syncthreads();
     hook();
-    srun_tail<N, B, T, SIGN, 1>(a, b, out, tw);
+    srun_tail<N, T, Geo, SIGN, 1>(a, b, out, tw);
 }
 
 // Same, with the result left in shared memory; returns the buffer holding it.
-template <int N, int B, int T, int SIGN, class In, class Hook>
+template <int N, int T, class Geo, int SIGN, class In, class Hook>
 __device__ __forceinline__ float2* srun_smem(const In& in, float2* a, float2* b, const float2* __restrict__ tw,
                                              const Hook& hook) {
     constexpr StaticPlan P = static_plan(N);
     float2* res = ((P.nr - 1) % 2 == 1) ? b : a;
-    srun_out<N, B, T, SIGN>(in, SSmem<B>{res}, a, b, tw, hook);
+    srun_out<N, T, Geo, SIGN>(in, SSmem<Geo>{res}, a, b, tw, hook);
     return res;
+}
+
+// Radix order of a transform: the default plan of N, or three given radices.
+// Any order computes the same transform (the Stockham passes accumulate LS);
+// orders are chosen so that the in-place passes hold few values per thread.
+template <int N, int R0 = 0, int R1 = 0, int R2 = 0>
+struct PlanOf {
+    static constexpr StaticPlan P = R0 ? StaticPlan{true, 3, {R0, R1, R2}} : static_plan(N);
+    static_assert(R0 == 0 || R0 * R1 * R2 == N, "radices must multiply to N");
+};
+
+// In-place pass: every butterfly of the thread is loaded into registers, the
+// block synchronises, then the butterflies are computed and stored over the
+// same buffer.  A tile then needs one working buffer instead of a ping-pong
+// pair; the registers hold N NL / T values per thread.
+template <int N, int T, class Geo, int R, int LS, int SIGN, class In, class Out>
+__device__ __forceinline__ void spass_ip(const In& in, const Out& out, const float2* __restrict__ tw) {
+    constexpr int NBL = N / R;
+    constexpr int NB = NBL * Geo::NL;
+    constexpr int IT = (NB + T - 1) / T;
+    constexpr int TWS = N / (LS * R) * Geo::TWM;
+    float2 v[IT][R];
+    auto coords = [](unsigned b, int& l, int& j) {
+        if constexpr (Geo::LF) {
+            l = (int)(b % Geo::NL);
+            j = (int)(b / Geo::NL);
+        } else {
+            l = (int)(b / NBL);
+            j = (int)(b - (unsigned)l * NBL);
+        }
+    };
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        if (NB % T == 0 || it < IT - 1 || b < (unsigned)NB) {
+            int l, j;
+            coords(b, l, j);
+            in.template load<R, NBL>(l, j, v[it]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        if (NB % T != 0 && it == IT - 1 && b >= (unsigned)NB) break;
+        int l, j;
+        coords(b, l, j);
+        const int jq = (int)((unsigned)j / LS);
+        const int k = j - jq * LS;
+        if constexpr (LS > 1) {
+            const int step = k * TWS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * step];
+                if (SIGN > 0) w.y = -w.y;
+                v[it][r] = cmul(v[it][r], w);
+            }
+        }
+        SmallDft<R>::run(v[it], SIGN);
+        out.template store<R, LS>(l, jq * LS * R + k, v[it]);
+    }
+}
+
+// passes S .. nr-1 in the single buffer a: in place, the last one into `out`
+// (in place as well when LAST_IP, i.e. `out` is a itself)
+template <int N, int T, class Geo, int SIGN, int S, bool LAST_IP, class PL, class Out>
+__device__ __forceinline__ void sip_tail(float2* a, const Out& out, const float2* __restrict__ tw) {
+    constexpr StaticPlan P = PL::P;
+    constexpr int R = P.r[S];
+    constexpr int LS = plan_ls(P, S);
+    if constexpr (S == P.nr - 1) {
+        if constexpr (LAST_IP)
+            spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
+        else
+            spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
+        __syncthreads();
+    } else {
+        spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{a}, tw);
+        __syncthreads();
+        sip_tail<N, T, Geo, SIGN, S + 1, LAST_IP, PL>(a, out, tw);
+    }
+}
+
+// Transform with one working buffer a: the first pass reads `in` (another
+// buffer, or a itself when FIRST_IP) into a, then `hook`, the other passes run
+// in place and the last writes `out` (a itself when LAST_IP).  Returns
+// synchronised.
+template <int N, int T, class Geo, int SIGN, bool FIRST_IP, bool LAST_IP, class PL = PlanOf<N>, class In, class Out,
+          class Hook>
+__device__ __forceinline__ void sip_run(const In& in, const Out& out, float2* a, const float2* __restrict__ tw,
+                                        const Hook& hook) {
+    constexpr StaticPlan P = PL::P;
+    static_assert(P.ok && P.nr >= 2, "specialised transforms need two or more passes");
+    if constexpr (FIRST_IP)
+        spass_ip<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
+    else
+        spass<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
+    __syncthreads();
+    hook();
+    sip_tail<N, T, Geo, SIGN, 1, LAST_IP, PL>(a, out, tw);
 }
 
 // Stage an N x B tile (row i at g + i S, B adjacent complex columns) into the
@@ -215,17 +338,59 @@ struct SYZStore {
     }
 };
 
+// i k_x times a spectrum tile read from shared memory (x component of the force)
+template <int N, class Geo>
+struct IkxLoad {
+    float2* p;
+    float kf;
+    template <int R, int D>
+    __device__ __forceinline__ void load(int l, int i0, float2* v) const {
+        SSmem<Geo>{p}.template load<R, D>(l, i0, v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r * D;
+            const float kx = (i == N / 2) ? 0.f : kf * (float)(i < N / 2 ? i : i - N);
+            v[r] = make_float2(-kx * v[r].y, kx * v[r].x);
+        }
+    }
+};
+
+// Radix orders of the two-buffer fused pass's transforms (forward, F_x, Psi).
+// In-place passes may hold at most N B / T values per thread; a radix whose
+// butterflies do not spread evenly over the threads goes where its pass is out
+// of place (the forward's and F_x's first pass, Psi's last).
+template <int N>
+struct GreenPlans {
+    using F = PlanOf<N>;
+    using I1 = PlanOf<N>;
+    using I2 = PlanOf<N>;
+};
+template <>
+struct GreenPlans<1536> {
+    using F = PlanOf<1536, 12, 8, 16>;
+    using I1 = PlanOf<1536, 12, 8, 16>;
+    using I2 = PlanOf<1536, 16, 8, 12>;
+};
+template <>
+struct GreenPlans<768> {
+    using F = PlanOf<768, 12, 4, 16>;
+    using I1 = PlanOf<768, 12, 4, 16>;
+    using I2 = PlanOf<768, 16, 4, 12>;
+};
+
 // strided complex pass (y: S = row stride, outer = x; or x on a plain mesh):
-// persistent blocks, cp.async prefetch of the next tile during this one
+// persistent blocks; the first pass reads the staged tile into the working
+// buffer, after which the next tile is staged with cp.async while the other
+// passes run in place
 template <int N, int B, int T, int SIGN>
-__global__ void __launch_bounds__(T) k_fft_strided_s(float2* data, LineGeom lg, int nct, int ntiles,
+__global__ void __launch_bounds__(T, 1) k_fft_strided_s(float2* data, LineGeom lg, int nct, int ntiles,
                                                       const float2* __restrict__ tw) {
+    using Geo = ColTile<B>;
     constexpr int TSZ = spad(N) * B;
     extern __shared__ float2 sm[];
     float2* stg = sm;
     float2* A = sm + TSZ;
-    float2* Bf = A + TSZ;
-    float2* tws = Bf + TSZ;
+    float2* tws = A + TSZ;
     for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
     const SCol rows{nullptr, lg.S};
     auto tile_base = [&](int t) {
@@ -243,17 +408,91 @@ __global__ void __launch_bounds__(T) k_fft_strided_s(float2* data, LineGeom lg, 
         auto next = [&]() {
             if (tn < ntiles) stile_prefetch<N, B, T>(stg, tile_base(tn), rows);
         };
-        srun_out<N, B, T, SIGN>(SSmem<B>{stg}, SCol{tile_base(t), lg.S}, A, Bf, tws, next);
+        sip_run<N, T, Geo, SIGN, false, false>(SSmem<Geo>{stg}, SCol{tile_base(t), lg.S}, A, tws, next);
     }
 }
 
 // x pass fused with the Poisson solve and the ik gradient on the interleaved,
 // x-blocked force mesh (the runtime form is k_fft_x_green): forward x FFT of
-// delta_k (component 0), phi = gscale delta_k / k^2 (times the radial filter
-// if given), F_x = IFFT_x(i k_x phi) and Psi = IFFT_x(phi) stored as
-// F_y = i k_y Psi, F_z = i k_z Psi.
+// delta_k (component 0) from the staged tile into A, phi = gscale delta_k / k^2
+// (times the radial filter if given) in place, F_x = IFFT_x(i k_x phi) worked
+// in the staging buffer, then (the next tile staged meanwhile) Psi =
+// IFFT_x(phi) in place in A, stored as F_y = i k_y Psi and F_z = i k_z Psi.
 template <int N, int B, int T>
-__global__ void __launch_bounds__(T) k_fft_x_green_s(float2* F, int nct, int ntiles, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(T, 1) k_fft_x_green_s(float2* F, int nct, int ntiles, const float2* __restrict__ tw,
+                                                      float gscale, float kf, const float* __restrict__ filt,
+                                                      int nfilt, float fstep) {
+    using G = XGeom<N>;
+    using Geo = ColTile<B>;
+    constexpr int TSZ = spad(N) * B;
+    constexpr int TB = T / B;    // line-element stride between a thread's spectrum values
+    constexpr int EPT = N / TB;  // spectrum values per thread
+    static_assert(T % B == 0 && N % TB == 0, "tile must split evenly over the block");
+    constexpr int half = N / 2;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = sm + TSZ;
+    float2* tws = A + TSZ;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    const int c = threadIdx.x % B;   // this thread's column in the Green phase
+    const int i0 = threadIdx.x / B;  // and its first line element: i = i0 + q TB
+    auto elem = [&](float2* base, int q) -> float2& {
+        if constexpr (TB % 16 == 0)
+            return base[c + spad(i0) * B + q * spad(TB) * B];
+        else
+            return base[c + spad(i0 + q * TB) * B];
+    };
+    auto tile_off = [&](int t) {
+        const int iy = t / nct;
+        return (long long)iy * G::RS + (long long)(t - iy * nct) * B;
+    };
+    const XOff<N> xo{};
+    int t = blockIdx.x;
+    if (t < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(t), xo);
+    for (; t < ntiles; t += gridDim.x) {
+        const int iy = t / nct;
+        const int col0 = (t - iy * nct) * B;
+        const long long off = (long long)iy * G::RS + col0;
+        cp_async_wait_all();
+        __syncthreads();
+        sip_run<N, T, Geo, -1, false, true, typename GreenPlans<N>::F>(SSmem<Geo>{stg}, SSmem<Geo>{A}, A, tws,
+                                                                      NoHook{});
+        const float ky = kf * (float)(iy < half ? iy : iy - N);
+        const float kz = kf * (float)(col0 + c);
+        const float kyz2 = ky * ky + kz * kz;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int i = i0 + q * TB;
+            const float kx = kf * (float)(i < half ? i : i - N);
+            const float k2 = kx * kx + kyz2;
+            float gk = k2 > 0.f ? gscale / k2 : 0.f;
+            if (filt) {
+                // radial transfer T(|k|), piecewise linear on nodes b * fstep
+                const float u = sqrtf(k2) / fstep;
+                int b = (int)u;
+                if (b > nfilt - 2) b = nfilt - 2;
+                const float f = fminf(u - (float)b, 1.f);
+                gk *= (1.f - f) * filt[b] + f * filt[b + 1];
+            }
+            float2& x = elem(A, q);
+            x = cscale(x, gk);
+        }
+        __syncthreads();
+        sip_run<N, T, Geo, +1, false, false, typename GreenPlans<N>::I1>(IkxLoad<N, Geo>{A, kf}, SXIO<N>{F + off}, stg,
+                                                                         tws, NoHook{});
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(tn), xo);
+        const float ky_eff = (iy == half) ? 0.f : ky;
+        sip_run<N, T, Geo, +1, true, false, typename GreenPlans<N>::I2>(SSmem<Geo>{A}, SYZStore<N>{F + off + G::P, F + off + 2 * G::P, ky_eff, kf, col0},
+                                            A, tws, NoHook{});
+    }
+}
+
+// The same fused pass with three tile buffers (staging + ping-pong) and phi
+// kept in registers: the next tile is staged during all three transforms, at
+// the cost of half the columns per tile of the two-buffer form.
+template <int N, int B, int T>
+__global__ void __launch_bounds__(T, 1) k_fft_x_green3_s(float2* F, int nct, int ntiles, const float2* __restrict__ tw,
                                                       float gscale, float kf, const float* __restrict__ filt,
                                                       int nfilt, float fstep) {
     using G = XGeom<N>;
@@ -293,7 +532,7 @@ __global__ void __launch_bounds__(T) k_fft_x_green_s(float2* F, int nct, int nti
         auto next = [&]() {
             if (tn < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(tn), xo);
         };
-        float2* X = srun_smem<N, B, T, -1>(SSmem<B>{stg}, A, W, tws, next);
+        float2* X = srun_smem<N, T, ColTile<B>, -1>(SSmem<ColTile<B>>{stg}, A, W, tws, next);
         const float ky = kf * (float)(iy < half ? iy : iy - N);
         const float kz = kf * (float)(col0 + c);
         const float kyz2 = ky * ky + kz * kz;
@@ -323,31 +562,243 @@ __global__ void __launch_bounds__(T) k_fft_x_green_s(float2* F, int nct, int nti
             elem(A, q) = make_float2(-kx * phi[q].y, kx * phi[q].x);  // i k_x phi
         }
         __syncthreads();
-        srun_out<N, B, T, +1>(SSmem<B>{A}, SXIO<N>{F + off}, W, A, tws, NoHook{});
+        srun_out<N, T, ColTile<B>, +1>(SSmem<ColTile<B>>{A}, SXIO<N>{F + off}, W, A, tws, NoHook{});
 #pragma unroll
         for (int q = 0; q < EPT; ++q) elem(A, q) = phi[q];
         __syncthreads();
-        srun_out<N, B, T, +1>(SSmem<B>{A}, SYZStore<N>{F + off + G::P, F + off + 2 * G::P, ky_eff, kf, col0}, W, A,
+        srun_out<N, T, ColTile<B>, +1>(SSmem<ColTile<B>>{A}, SYZStore<N>{F + off + G::P, F + off + 2 * G::P, ky_eff, kf, col0}, W, A,
                               tws, NoHook{});
     }
 }
 
 template <int N, int B, int T>
+constexpr size_t line_pass_smem() {
+    return ((size_t)2 * spad(N) * B + N) * 8;
+}
+
+template <int N, int B, int T>
 inline int run_strided(float2* data, int sign, LineGeom lg, int nct, int ntiles, const float2* tw, cudaStream_t s) {
-    const size_t smem = ((size_t)3 * spad(N) * B + N) * 8;
+    constexpr size_t smem = line_pass_smem<N, B, T>();
     auto kern = sign < 0 ? k_fft_strided_s<N, B, T, -1> : k_fft_strided_s<N, B, T, +1>;
     if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
     kern<<<persistent_grid(smem, ntiles), T, smem, s>>>(data, lg, nct, ntiles, tw);
     return check_launch();
 }
 
-template <int N, int B, int T>
+// NBUF = 2: k_fft_x_green_s (in-place passes), 3: k_fft_x_green3_s
+template <int N, int B, int T, int NBUF>
 inline int run_x_green(float2* F, int nct, int ntiles, const float2* tw, float gscale, float kf, const float* filt,
                        int nfilt, float fstep, cudaStream_t s) {
-    const size_t smem = ((size_t)3 * spad(N) * B + N) * 8;
-    if (!set_smem((const void*)k_fft_x_green_s<N, B, T>, smem)) return COLA_ECUDA;
-    k_fft_x_green_s<N, B, T><<<persistent_grid(smem, ntiles), T, smem, s>>>(F, nct, ntiles, tw, gscale, kf, filt,
-                                                                             nfilt, fstep);
+    constexpr size_t smem = ((size_t)NBUF * spad(N) * B + N) * 8;
+    auto kern = [] {
+        if constexpr (NBUF == 2)
+            return k_fft_x_green_s<N, B, T>;
+        else
+            return k_fft_x_green3_s<N, B, T>;
+    }();
+    if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
+    kern<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep);
+    return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// z passes (rows of the mesh, real <-> half-complex): persistent blocks over
+// tiles of NR rows; the next tile's rows are staged into shared memory with
+// cp.async while this one is transformed.
+// ---------------------------------------------------------------------------
+// c2r pre-processing from a staged row X[0..M]:
+// Z[k] = (X[k] + conj X[M-k]) + i (X[k] - conj X[M-k]) W_2M^-k, Im X[0], Im X[M] ignored
+template <int M, int SP>
+struct C2rStage {
+    const float2* stg;
+    const float2* tw;  // exp(-2 pi i q / 2M)
+    template <int R, int D>
+    __device__ __forceinline__ void load(int l, int i0, float2* v) const {
+        const float2* x = stg + l * SP;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = i0 + r * D;
+            float2 a = x[k], bb = x[M - k];
+            if (k == 0) {
+                a.y = 0.f;
+                bb.y = 0.f;
+            }
+            const float2 b = cconj(bb);
+            float2 w = tw[k];
+            w.y = -w.y;
+            const float2 d = cmul(csub(a, b), w);
+            v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
+        }
+    }
+};
+
+// row output (in place): z[m] as the float pair (2m, 2m+1) of row row0 + l
+struct SRowStore {
+    float2* data;
+    long long rs, row0, nrows;
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l, int i0, const float2* v) const {
+        const long long row = row0 + l;
+        if (row >= nrows) return;
+        float2* q = data + row * rs + i0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(q + r * D, v[r]);
+    }
+};
+
+// fixed-point CIC counts (2^40 per particle, staged rows of N) -> packed
+// complex pairs of delta = count scale - 1
+template <int N>
+struct FixStage {
+    const unsigned long long* stg;
+    float scale;
+    template <int R, int D>
+    __device__ __forceinline__ void load(int l, int i0, float2* v) const {
+        const ulonglong2* x = reinterpret_cast<const ulonglong2*>(stg + (size_t)l * N);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const ulonglong2 c = x[i0 + r * D];
+            v[r] = make_float2((float)c.x * scale - 1.0f, (float)c.y * scale - 1.0f);
+        }
+    }
+};
+
+template <int N, int NR, int T>
+constexpr size_t z_c2r_smem() {
+    return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + N) * 8;
+}
+template <int N, int NR, int T>
+constexpr size_t z_r2c_smem() {
+    return ((size_t)NR * N + 2 * (size_t)NR * (spad(N / 2) + 1) + N) * 8;
+}
+
+// inverse c2r along z, in place on rows of rs complex (the runtime form is
+// k_fft_z_c2r<false>): the staged rows are pre-processed in the first pass's
+// loads, the passes ping-pong between two buffers, twiddles in shared memory
+template <int N, int NR, int T, int MB>
+__global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long rs, long long nrows, int ntiles,
+                                                        const float2* __restrict__ tw) {
+    constexpr int M = N / 2;
+    using Geo = RowTile<M, NR>;
+    constexpr int SP = M + 2;  // staged row: X[0..M], whole 16-byte chunks
+    constexpr int HS = SP / 2;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = stg + NR * SP;
+    float2* Bf = A + NR * Geo::LSTR;
+    float2* tws = Bf + NR * Geo::LSTR;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    auto prefetch = [&](int t) {
+        const long long row0 = (long long)t * NR;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NR * HS; e += T) {
+            const int l = e / HS, c = (e - l * HS) * 2;
+            if (row0 + l < nrows) cp_async16(stg + l * SP + c, data + (row0 + l) * rs + c);
+        }
+        cp_async_commit();
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) prefetch(t);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int tn = t + gridDim.x;
+        auto next = [&]() {
+            if (tn < ntiles) prefetch(tn);
+        };
+        srun_out<M, T, Geo, +1>(C2rStage<M, SP>{stg, tws}, SRowStore{data, rs, (long long)t * NR, nrows}, A, Bf, tws,
+                                next);
+    }
+}
+
+// forward r2c along z of the fixed-point CIC mesh (rows of N counts), which
+// is cleared as it is consumed; output row r = x n + y to frow(x, y, 0, fr)
+// (the runtime form is k_fft_z_r2c<true>)
+template <int N, int NR, int T, int MB>
+__global__ void __launch_bounds__(T, MB) k_fft_z_r2c_fix_s(unsigned long long* __restrict__ dep, float2* out,
+                                                            long long rs, long long nrows, int ntiles, float scale,
+                                                            const float2* __restrict__ tw, FRow fr) {
+    constexpr int M = N / 2;
+    using Geo = RowTile<M, NR>;
+    constexpr int HN = N / 2;  // 16-byte chunks per count row
+    extern __shared__ float2 sm[];
+    __shared__ long long obase[NR];
+    unsigned long long* stg = reinterpret_cast<unsigned long long*>(sm);
+    float2* A = sm + NR * N;
+    float2* Bf = A + NR * Geo::LSTR;
+    float2* tws = Bf + NR * Geo::LSTR;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    auto prefetch = [&](int t) {
+        const long long row0 = (long long)t * NR;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NR * HN; e += T) {
+            const int l = e / HN, c = (e - l * HN) * 2;
+            if (row0 + l < nrows) cp_async16(stg + (size_t)l * N + c, dep + (row0 + l) * N + c);
+        }
+        cp_async_commit();
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) prefetch(t);
+    for (; t < ntiles; t += gridDim.x) {
+        const long long row0 = (long long)t * NR;
+        cp_async_wait_all();
+        __syncthreads();
+        // the counts of this tile are in shared memory: clear them in the mesh
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NR * HN; e += T) {
+            const int l = e / HN, c = (e - l * HN) * 2;
+            if (row0 + l < nrows)
+                __stcs(reinterpret_cast<ulonglong2*>(dep + (row0 + l) * N + c), make_ulonglong2(0ull, 0ull));
+        }
+        if (threadIdx.x < NR) {
+            const long long r = row0 + threadIdx.x;
+            const int x = (int)(r / N), y = (int)(r - (long long)x * N);
+            obase[threadIdx.x] = frow(x, y, 0, fr) * rs;
+        }
+        const int tn = t + gridDim.x;
+        auto next = [&]() {
+            if (tn < ntiles) prefetch(tn);
+        };
+        const float2* Z = srun_smem<M, T, Geo, -1>(FixStage<N>{stg, scale}, A, Bf, tws, next);
+        // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / (2i)
+#pragma unroll 2
+        for (int e = threadIdx.x; e < NR * (M + 1); e += T) {
+            const int l = e / (M + 1), k = e - l * (M + 1);
+            if (row0 + l >= nrows) continue;
+            const float2 a = Z[l * Geo::LSTR + spad(k == M ? 0 : k)];
+            const float2 b = cconj(Z[l * Geo::LSTR + spad(k == 0 ? 0 : M - k)]);
+            const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            const float2 D = csub(a, b);
+            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+            __stcs(out + obase[l] + k, cadd(E, cmul(tws[k], O)));
+        }
+    }
+}
+
+// MB: resident blocks per SM the kernel is compiled for (registers per thread
+// at most 65536 / (MB T)); shared memory must allow as many
+template <int N, int NR, int T, int MB>
+inline int run_z_c2r(float2* data, long long rs, long long nrows, const float2* tw, cudaStream_t s) {
+    static_assert(fft_pitch(N) >= N / 2 + 2, "staged rows must fit the row pitch");
+    constexpr size_t smem = z_c2r_smem<N, NR, T>();
+    static_assert((smem + 1024) * MB <= 227 * 1024, "MB blocks must fit in shared memory");
+    const long long nt = (nrows + NR - 1) / NR;
+    if (nt > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
+    if (!set_smem((const void*)k_fft_z_c2r_s<N, NR, T, MB>, smem)) return COLA_ECUDA;
+    k_fft_z_c2r_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt), T, smem, s>>>(data, rs, nrows, (int)nt, tw);
+    return check_launch();
+}
+
+template <int N, int NR, int T, int MB>
+inline int run_z_r2c_fix(unsigned long long* dep, float2* out, long long rs, long long nrows, float scale,
+                         const float2* tw, FRow fr, cudaStream_t s) {
+    constexpr size_t smem = z_r2c_smem<N, NR, T>();
+    static_assert((smem + 64 * NR + 1024) * MB <= 227 * 1024, "MB blocks must fit in shared memory");
+    const long long nt = (nrows + NR - 1) / NR;
+    if (nt > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
+    if (!set_smem((const void*)k_fft_z_r2c_fix_s<N, NR, T, MB>, smem)) return COLA_ECUDA;
+    k_fft_z_r2c_fix_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt), T, smem, s>>>(dep, out, rs, nrows, (int)nt,
+                                                                                     scale, tw, fr);
     return check_launch();
 }
 
@@ -357,6 +808,20 @@ bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, in
                            const float2* tw, cudaStream_t s, int* rc);
 bool launch_x_green_static(float2* F, int n, int B, int nct, int ntiles, const float2* tw, float gscale, float kf,
                            const float* filt, int nfilt, float fstep, cudaStream_t s, int* rc);
+// z passes of the step: the in-place c2r of the force rows and the r2c of the
+// fixed-point counts (fft_spec_large.cu)
+bool launch_z_c2r_static(float2* data, int n, long long rs, long long nrows, const float2* tw, cudaStream_t s,
+                         int* rc);
+bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long long rs, long long nrows,
+                             float scale, const float2* tw, FRow fr, cudaStream_t s, int* rc);
+// default column width of the specialised line passes for n (0: none)
+int static_tile(int n);
+// whether (n, B) has specialised line passes
+bool static_tile_ok(int n, int B);
+// default column width of the specialised fused x/Green pass for n (0: the
+// strided passes' width)
+int static_green_tile(int n);
+int launch_static_green_tile_small(int n);
 // the mesh sizes below 512 (batched ensembles, tests), in fft_spec_small.cu
 bool launch_strided_static_small(float2* data, int n, int B, int sign, LineGeom lg, int nct, int ntiles,
                                  const float2* tw, cudaStream_t s, int* rc);

@@ -136,7 +136,7 @@ def torch_pm_force(d, nq, ng, L, green, chunk=1 << 23):
     return out
 
 
-@pytest.mark.parametrize("nq,ng,L", [(256, 768, 768.0), (NQ, NG, L)])
+@pytest.mark.parametrize("nq,ng,L", [(256, 768, 768.0), (384, 1152, 1152.0), (NQ, NG, L)])
 def test_force_matches_library_fft_reference(nq, ng, L):
     a = 0.5
     d = dev(random_displacements(5, nq, 0.7 * L / nq))
@@ -150,3 +150,4 @@ def test_force_matches_library_fft_reference(nq, ng, L):
     ref = torch_pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / a)
     rel = (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item()
     assert rel < 1e-5, rel
+
