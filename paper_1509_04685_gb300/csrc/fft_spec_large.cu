@@ -53,7 +53,7 @@ static const int kStaticTiles[][2] = {{96, 16}, {128, 16}, {160, 16}, {192, 16},
 static const int kStaticSpecs[][2] = {{96, 16}, {128, 16}, {160, 16}, {192, 16}, {256, 16}, {256, 8}, {288, 16}, {320, 16}, {384, 16}, {384, 8}, {480, 16}, {480, 8}, {768, 16}, {768, 8}, {1152, 8}, {1536, 8}, {2304, 4}};
 
 // default column width of the specialised fused x/Green pass of each size
-static const int kGreenTiles[][2] = {{768, 8}, {1152, 4}, {1536, 8}, {2304, 2}};
+static const int kGreenTiles[][2] = {{768, 8}, {1152, 8}, {1536, 8}, {2304, 4}};
 
 int static_green_tile(int n) {
     for (const auto& e : kGreenTiles)
@@ -73,36 +73,43 @@ bool static_tile_ok(int n, int B) {
     return false;
 }
 
-// (n, rows per tile, threads, blocks per SM of the c2r and the r2c kernel) of
-// the z-pass specialisations
-#define COLA_Z_SPECS(X)        \
-    X(256, 16, 256, 1, 1)      \
-    X(384, 8, 128, 1, 1)       \
-    X(768, 8, 256, 2, 2)       \
-    X(1152, 4, 256, 2, 2)      \
-    X(1536, 4, 256, 2, 2)      \
-    X(2304, 2, 256, 2, 2)
+// (n, rows per tile, threads, blocks per SM) of the z-pass specialisations
+#define COLA_ZC2R_SPECS(X)   \
+    X(256, 16, 256, 1)       \
+    X(384, 8, 128, 1)        \
+    X(768, 8, 256, 2)        \
+    X(1152, 4, 256, 2)       \
+    X(1536, 4, 256, 2)       \
+    X(2304, 2, 256, 2)
+
+#define COLA_ZR2C_SPECS(X)   \
+    X(256, 16, 256, 1)       \
+    X(384, 8, 128, 1)        \
+    X(768, 8, 256, 2)        \
+    X(1152, 4, 256, 2)       \
+    X(1536, 4, 256, 2)       \
+    X(2304, 2, 256, 2)
 
 bool launch_z_c2r_static(float2* data, int n, long long rs, long long nrows, const float2* tw, cudaStream_t s,
                          int* rc) {
-#define COLA_CASE(NN, RR, TT, MC, MR)                        \
-    if (n == NN) {                                           \
-        *rc = run_z_c2r<NN, RR, TT, MC>(data, rs, nrows, tw, s); \
-        return true;                                         \
+#define COLA_CASE(NN, RR, TT, MB)                                \
+    if (n == NN) {                                               \
+        *rc = run_z_c2r<NN, RR, TT, MB>(data, rs, nrows, tw, s); \
+        return true;                                             \
     }
-    COLA_Z_SPECS(COLA_CASE)
+    COLA_ZC2R_SPECS(COLA_CASE)
 #undef COLA_CASE
     return false;
 }
 
 bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long long rs, long long nrows,
                              float scale, const float2* tw, FRow fr, cudaStream_t s, int* rc) {
-#define COLA_CASE(NN, RR, TT, MC, MR)                                               \
+#define COLA_CASE(NN, RR, TT, MB)                                                   \
     if (n == NN) {                                                                  \
-        *rc = run_z_r2c_fix<NN, RR, TT, MR>(dep, out, rs, nrows, scale, tw, fr, s); \
+        *rc = run_z_r2c_fix<NN, RR, TT, MB>(dep, out, rs, nrows, scale, tw, fr, s); \
         return true;                                                                \
     }
-    COLA_Z_SPECS(COLA_CASE)
+    COLA_ZR2C_SPECS(COLA_CASE)
 #undef COLA_CASE
     return false;
 }

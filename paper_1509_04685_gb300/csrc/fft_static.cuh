@@ -673,8 +673,9 @@ constexpr size_t z_r2c_smem() {
 }
 
 // inverse c2r along z, in place on rows of rs complex (the runtime form is
-// k_fft_z_c2r<false>): the staged rows are pre-processed in the first pass's
-// loads, the passes ping-pong between two buffers, twiddles in shared memory
+// k_fft_z_c2r<false>): tiles of NR rows staged with cp.async; the first pass
+// pre-processes the staged rows, after which the next tile is staged while the
+// other passes ping-pong between two buffers
 template <int N, int NR, int T, int MB>
 __global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long rs, long long nrows, int ntiles,
                                                         const float2* __restrict__ tw) {
