@@ -38,6 +38,8 @@ WORKLOADS = {
     "small": dict(name="cola_32^3_particles_96^3_mesh_L128_40steps", nq=32, ng=96, box=128.0),
     # 48 seeds: 16 each at 96^3, 128^3, 160^3 particles, PM_grid cycling 1, 2, 3, L = 1 Mpc/h per spacing
     "ensemble": dict(name="cola_ensemble_48_seeds_96-128-160^3_pm1-2-3_40steps", nq=0, ng=0, box=0.0),
+    # learned 1x mesh vs plain 3x mesh, 256^3 particles, L = 512 Mpc/h
+    "learned": dict(name="cola_learned_256^3_particles_256^3_vs_768^3_mesh_L512_40steps", nq=0, ng=0, box=0.0),
 }
 
 
@@ -111,6 +113,92 @@ def run_ensemble(args, rank, world, C, torch, dist):
                        "parallelism": f"members sharded over {world} rank(s)"},
             "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
         }), flush=True)
+def run_learned(args, rank, world, C, torch, dist):
+    """The learned 1x-mesh form against the plain 3x-mesh form: 256^3
+    particles, L = 512 Mpc/h, 40 steps.  The correction is fitted on seeded
+    plain 3x runs (filter rows from every node of every run, the net on four
+    nodes of the first eight), then both forms run the held-out seeds.  The
+    value is the learned form's particle-steps/s; the line adds the plain 3x
+    form's, their ratio and the final P(k) deviation for k <= 1 h/Mpc."""
+    import numpy as np
+
+    from paper_1509_04685_gb300 import learn
+
+    nq, box = 256, 512.0
+    train_seeds = [1001 + 100 * rank + i for i in range(args.learned_train)]
+    test_seeds = [2001 + 100 * rank + i for i in range(args.learned_test)]
+    t0 = time.perf_counter()
+    corr = learn.LearnedCorrection(nfilter=16, seed=0, nfilter_a=8)
+    samples, final = learn.fit_filter_runs(corr, train_seeds, nq, box, keep_nodes=(10, 20, 30, 39))
+    samples = samples[: 4 * 8]
+    hist = learn.train(corr, samples, nq, box, iters=args.learned_iters, lr=3e-3,
+                       log_every=max(1, args.learned_iters // 4))
+    del samples
+    torch.cuda.empty_cache()
+    gain, boost = learn.calibrate_filter(corr, {s: final[s] for s in train_seeds[:4]}, nq, box)
+    t_train = time.perf_counter() - t0
+    cfg3 = C.make_config(nq, 3 * nq, box, A_INIT, 1.0, N_NODES)
+    cfg1 = C.make_config(nq, nq, box, A_INIT, 1.0, N_NODES)
+    cfgl = corr.config(nq, box)
+    sims = {"plain_3x": C.Simulation(cfg3), "plain_1x": C.Simulation(cfg1), "learned_1x": C.Simulation(cfgl)}
+    ms = {k: 0.0 for k in sims}
+    pk = {k: [] for k in sims}
+    launches0 = C.cola_launch_count()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for key, sm in sims.items():  # one untimed run per form (kernel attributes, caches)
+        sm.ic(test_seeds[0])
+        sm.run()
+    for seed in test_seeds:
+        for key, sm in sims.items():
+            sm.ic(seed)
+            torch.cuda.synchronize()
+            e0.record()
+            sm.run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms[key] += e0.elapsed_time(e1)
+            if sm.status() != 0:
+                raise SystemExit(f"device status after the {key} run")
+            k, p, _ = sm.power(nq, node=N_NODES - 1)
+            pk[key].append(p.cpu().numpy())
+    clk = clocks.stop()
+    k = k.cpu().numpy()
+    sel = k <= 1.0
+    ratio = {key: np.mean(np.stack(pk[key]), axis=0) / np.mean(np.stack(pk["plain_3x"]), axis=0) for key in pk}
+    dev = {key: float(np.max(np.abs(ratio[key][sel] - 1))) for key in ("plain_1x", "learned_1x")}
+    mdev = {key: float(np.mean(np.abs(ratio[key][(k > 0.1) & sel] - 1))) for key in ("plain_1x", "learned_1x")}
+    nsteps = N_NODES * len(test_seeds)
+    ps = {key: nq**3 * nsteps / (ms[key] * 1e-3) for key in ms}
+    tot = torch.tensor([ps["learned_1x"], ps["plain_3x"]], device="cuda")
+    if dist:
+        dist.all_reduce(tot)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "particle-steps/s of the learned 1x-mesh form (256^3 particles, L=512 Mpc/h)",
+            "value": float(tot[0].item()), "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": N_NODES,
+            "ms_per_step": ms["learned_1x"] / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bf16 convolutions)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["learned"]["name"], "nq": nq, "ng_learned": nq, "ng_plain": 3 * nq,
+                       "box": box, "n_steps": N_NODES, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
+                       "filter": "16 radial nodes x 8 scale-factor rows, least squares on every node of the fine runs, "
+                                 "boost calibrated on 4 training seeds' final P(k)", "net_iters": args.learned_iters,
+                       "parallelism": f"replicas{world}"},
+            "plain_3x": {"value": float(tot[1].item()), "ms_per_step": ms["plain_3x"] / nsteps},
+            "plain_1x": {"ms_per_step": ms["plain_1x"] / nsteps},
+            "speedup_vs_plain_3x": ps["learned_1x"] / ps["plain_3x"],
+            "pk_final": {"k_max": 1.0, "target_max_abs_dev": 0.01,
+                         "max_abs_dev": dev, "mean_abs_dev_0.1_to_1": mdev,
+                         "learned_within_target": dev["learned_1x"] <= 0.01,
+                         "ratio_learned": [round(float(x), 5) for x in ratio["learned_1x"][sel]],
+                         "ratio_plain_1x": [round(float(x), 5) for x in ratio["plain_1x"][sel]],
+                         "k": [round(float(x), 4) for x in k[sel]]},
+            "training": {"seconds": t_train, "loss": hist, "filter_gain": gain, "filter_boost": boost,
+                         "calibration_seeds": 4},
+            "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
+        }), flush=True)
+
+
 A_INIT, N_NODES = 0.05, 40
 METRIC = "particle-steps/s at 512^3/1536^3"
 METRICS = {"largest": "particle-steps/s at 768^3/2304^3", "mid": "particle-steps/s at 256^3/768^3",
@@ -282,6 +370,9 @@ def main():
     ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=32, help="fine training runs (learned workload)")
+    ap.add_argument("--learned-test", type=int, default=8, help="held-out seeds (learned workload)")
+    ap.add_argument("--learned-iters", type=int, default=300, help="Adam iterations of the net (learned workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -303,8 +394,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    if args.workload == "ensemble":
-        run_ensemble(args, rank, world, C, torch, dist)
+    if args.workload in ("ensemble", "learned"):
+        (run_ensemble if args.workload == "ensemble" else run_learned)(args, rank, world, C, torch, dist)
         if dist:
             dist.destroy_process_group()
         return

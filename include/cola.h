@@ -66,7 +66,10 @@ typedef struct cola_cosmology {
  * COLA_FLAG_LEARNED, typically on a PM_grid = 1 mesh).  The force mesh is
  *   F = IFFT(T(|k|) F_k) + g net(delta, F/g),   g = 3/2 Om/a,
  * with T a radial transfer function (piecewise linear on nfilter nodes
- * k_b = b sqrt(3) pi ng / (L (nfilter - 1)); NULL means T = 1) and net three
+ * k_b = b sqrt(3) pi ng / (L (nfilter - 1)); NULL means T = 1).  With
+ * nfilter_a > 1 the filter holds nfilter_a rows of nfilter values, row r for
+ * a_r = a_init + r (a_final - a_init) / (nfilter_a - 1), and a force at scale
+ * factor a uses the nearest row (nfilter_a <= 1: one row for all a).  net is three
  * circular 3x3x3 convolutions 4 -> 16 -> 16 -> 3 with ReLU, BF16 weights and
  * activations, FP32 accumulation.  params (device, FP32, COLA_NET_NPARAMS):
  *   W1 [16][4][27] @0, b1 [16] @1728, W2 [16][16][27] @1744, b2 [16] @8656,
@@ -80,6 +83,7 @@ typedef struct cola_net {
     void* wpack;
     const float* filter;
     int32_t nfilter;
+    int32_t nfilter_a;
 } cola_net;
 
 /* One simulation (Table 1's code parameters). */

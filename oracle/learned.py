@@ -96,6 +96,16 @@ def init_params(seed: int, cin=4, c=16, cout=3, scale=0.1):
             "W3": w(cout, c), "b3": np.zeros(cout)}
 
 
+def filter_row(a: float, nrows: int, a_init: float, a_final: float) -> int:
+    """Row of a scale-factor-dependent filter table used at scale factor a:
+    rows sit at a_r = a_init + r (a_final - a_init) / (nrows - 1) and the
+    nearest one is used (a single row for nrows <= 1)."""
+    if nrows <= 1:
+        return 0
+    nodes = a_init + np.arange(nrows) * (a_final - a_init) / (nrows - 1)
+    return int(np.argmin(np.abs(nodes - a)))
+
+
 def radial_bins(ng: int, L: float, nbins: int):
     """Piecewise-linear hat basis in |k| for the k-space filter: node b at
     k_b = b * k_max / (nbins - 1), k_max = sqrt(3) pi ng / L."""

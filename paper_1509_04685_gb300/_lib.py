@@ -36,7 +36,7 @@ class cola_cosmology(ctypes.Structure):
 
 class cola_net(ctypes.Structure):
     _fields_ = [("params", ctypes.c_void_p), ("wpack", ctypes.c_void_p), ("filter", ctypes.c_void_p),
-                ("nfilter", ctypes.c_int32)]
+                ("nfilter", ctypes.c_int32), ("nfilter_a", ctypes.c_int32)]
 
 
 class cola_config(ctypes.Structure):
@@ -140,8 +140,17 @@ def make_config(nq: int, ng: int, box: float, a_init: float, a_final: float = 1.
 
 def make_net(params, wpack, filt=None) -> cola_net:
     """Descriptor of a learned correction: params (device float[NET_NPARAMS]),
-    wpack (device bf16[NET_NPACK] storage), optional filter table (device float[n])."""
-    return cola_net(_ptr(params), _ptr(wpack), _ptr(filt), 0 if filt is None else int(filt.numel()))
+    wpack (device bf16[NET_NPACK] storage), optional filter table: device
+    float[nfilter], or float[nfilter_a, nfilter] with one row per scale-factor
+    node (rows spaced linearly from a_init to a_final of the config)."""
+    if filt is None:
+        net = cola_net(_ptr(params), _ptr(wpack), None, 0, 0)
+    elif filt.dim() == 2:
+        net = cola_net(_ptr(params), _ptr(wpack), _ptr(filt), int(filt.shape[1]), int(filt.shape[0]))
+    else:
+        net = cola_net(_ptr(params), _ptr(wpack), _ptr(filt), int(filt.numel()), 1)
+    net._tensors = (params, wpack, filt)  # the descriptor holds raw device pointers: keep the tensors alive
+    return net
 
 
 def cola_net_pack(net: cola_net, stream=None):

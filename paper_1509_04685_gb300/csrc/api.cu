@@ -32,6 +32,7 @@ static int check_config(const cola_config* c) {
         if (c->ng % 16) return COLA_EUNSUPPORTED_SIZE;  // conv bricks of 4 x 8 x 16 voxels
         if (!c->net || !c->net->params || !c->net->wpack) return COLA_EINVAL;
         if (c->net->filter && (c->net->nfilter < 2 || c->net->nfilter > 64)) return COLA_EINVAL;
+        if (c->net->filter && (c->net->nfilter_a < 0 || c->net->nfilter_a > kMaxSteps)) return COLA_EINVAL;
     }
     return COLA_OK;
 }
@@ -122,11 +123,24 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     return COLA_OK;
 }
 
+// filter row of the learned correction for scale factor a: the nearest of the
+// nfilter_a rows spaced linearly from a_init to a_final
+static const float* filter_row(const cola_config* cfg, double a) {
+    const cola_net* n = cfg->net;
+    if (!n->filter || n->nfilter_a <= 1) return n->filter;
+    const double u = (a - cfg->a_init) / (cfg->a_final - cfg->a_init) * (n->nfilter_a - 1);
+    int r = (int)std::floor(u + 0.5);
+    r = r < 0 ? 0 : (r > n->nfilter_a - 1 ? n->nfilter_a - 1 : r);
+    return n->filter + (size_t)r * n->nfilter;
+}
+
 static int pm_forces_for(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
                          cudaStream_t s) {
-    if (cfg->flags & COLA_FLAG_LEARNED)
-        return pm_mesh_forces(cfg, st, green, ws, L, s, cfg->net->filter, cfg->net->filter ? cfg->net->nfilter : 0,
+    if (cfg->flags & COLA_FLAG_LEARNED) {
+        const double a = 1.5 * cfg->cosmo.omega_m / green;
+        return pm_mesh_forces(cfg, st, green, ws, L, s, filter_row(cfg, a), cfg->net->filter ? cfg->net->nfilter : 0,
                               true);
+    }
     return pm_mesh_forces(cfg, st, green, ws, L, s);
 }
 

@@ -38,14 +38,24 @@ def init_params(seed: int, device="cuda") -> torch.Tensor:
     return p.to(device)
 
 
-class LearnedCorrection:
-    """Parameters, packed weights, filter table and Adam state of one net."""
+def filter_row(a: float, nrows: int, a_init: float = 0.05, a_final: float = 1.0) -> int:
+    """Row of a scale-factor-dependent filter table used at scale factor a:
+    the nearest of nrows nodes spaced linearly from a_init to a_final."""
+    if nrows <= 1:
+        return 0
+    u = (a - a_init) / (a_final - a_init) * (nrows - 1)
+    return int(min(max(np.floor(u + 0.5), 0), nrows - 1))
 
-    def __init__(self, nfilter: int = 16, seed: int = 0, device="cuda"):
+
+class LearnedCorrection:
+    """Parameters, packed weights, filter table and Adam state of one net.
+    The radial filter has nfilter_a rows, one per scale-factor node."""
+
+    def __init__(self, nfilter: int = 16, seed: int = 0, device="cuda", nfilter_a: int = 1):
         self.device = torch.device(device)
         self.params = init_params(seed, device)
         self.wpack = torch.zeros(L.NET_NPACK, dtype=torch.bfloat16, device=self.device)
-        self.filter = torch.ones(nfilter, dtype=torch.float32, device=self.device)
+        self.filter = torch.ones((nfilter_a, nfilter), dtype=torch.float32, device=self.device)
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.t = 0
@@ -97,21 +107,130 @@ def make_samples(seeds, nq: int, box: float, m_fine: int = 3, nodes=(10, 20, 30,
     return out
 
 
+class FilterFit:
+    """Normal equations of the least-squares radial filter, one system per
+    filter row (the gathered 1x-mesh force is linear in the node values)."""
+
+    def __init__(self, corr: LearnedCorrection, nq: int, box: float):
+        self.corr, self.nq, self.box = corr, nq, box
+        na, nb = corr.filter.shape
+        self.cfg = L.make_config(nq, nq, box, 0.05)
+        self.sim = Simulation(self.cfg, device=corr.device)
+        self.sim.init_tables()
+        self.basis = torch.empty((nb, 3 * nq**3), dtype=torch.float32, device=corr.device)
+        self.ATA = torch.zeros((na, nb, nb), dtype=torch.float64, device=corr.device)
+        self.ATy = torch.zeros((na, nb), dtype=torch.float64, device=corr.device)
+        self.count = [0] * na
+
+    def add(self, d, a: float, target):
+        """Accumulate one configuration: positions d, scale factor a, fine force."""
+        na, nb = self.corr.filter.shape
+        r = filter_row(a, na)
+        self.sim.d.copy_(d)
+        L.cola_filter_accumulate(self.cfg, self.sim.state, a, target, nb, self.basis, self.ATA[r], self.ATy[r],
+                                 self.sim.ws)
+        self.count[r] += 1
+
+    def solve(self, ridge: float = 1e-6):
+        na, nb = self.corr.filter.shape
+        for r in range(na):
+            if self.count[r]:
+                L.cola_filter_solve(self.ATA[r], self.ATy[r], nb, ridge, self.corr.filter[r])
+        torch.cuda.synchronize()
+        return self.corr.filter.clone()
+
+
 def fit_filter(corr: LearnedCorrection, samples, nq: int, box: float, ridge: float = 1e-6):
-    """Least-squares radial filter over all samples (normal equations summed)."""
-    nb = corr.filter.numel()
-    cfg = L.make_config(nq, nq, box, 0.05)
-    sim = Simulation(cfg, device=corr.device)
-    sim.init_tables()
-    basis = torch.empty((nb, 3 * nq**3), dtype=torch.float32, device=corr.device)
-    ATA = torch.zeros((nb, nb), dtype=torch.float64, device=corr.device)
-    ATy = torch.zeros(nb, dtype=torch.float64, device=corr.device)
+    """Least-squares radial filter over stored samples (normal equations summed per row)."""
+    fit = FilterFit(corr, nq, box)
     for s in samples:
-        sim.d.copy_(s.d)
-        L.cola_filter_accumulate(cfg, sim.state, s.a, s.force, nb, basis, ATA, ATy, sim.ws)
-    L.cola_filter_solve(ATA, ATy, nb, ridge, corr.filter)
+        fit.add(s.d, s.a, s.force)
+    return fit.solve(ridge)
+
+
+def fit_filter_runs(corr: LearnedCorrection, seeds, nq: int, box: float, m_fine: int = 3, a_init=0.05, n_steps=40,
+                    ridge: float = 1e-6, keep_nodes=(), device="cuda"):
+    """Least-squares filter from plain runs at PM_grid = m_fine, accumulated at
+    every node of every run without storing the configurations.  Returns the
+    Samples at keep_nodes (for the net) and each run's final P(k) on an nq^3
+    mesh, {seed: (k, P)}, as by-products."""
+    fit = FilterFit(corr, nq, box)
+    cfg = L.make_config(nq, m_fine * nq, box, a_init, 1.0, n_steps)
+    sim = Simulation(cfg, device=device)
+    kept, final = [], {}
+    for seed in seeds:
+        sim.ic(seed)
+        tab = sim.table()[:, 0].cpu().numpy()
+        for j in range(n_steps):
+            a = float(tab[j])
+            target = sim.force(a)
+            fit.add(sim.d, a, target)
+            if j in keep_nodes:
+                kept.append(Sample(sim.d.clone(), a, target.clone()))
+            sim.step(j)
+        k, p, _ = sim.power(nq, node=n_steps - 1)
+        final[seed] = (k.cpu().numpy(), p.cpu().numpy())
+    fit.solve(ridge)
+    del sim
+    return kept, final
+
+
+def pk_deviation(k, p, p_ref, kmax: float = 1.0):
+    """Mean |P / P_ref - 1| over the bins with k <= kmax."""
+    sel = k <= kmax
+    return float(np.mean(np.abs(p[sel] / p_ref[sel] - 1.0)))
+
+
+def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: float = 1.0, rounds: int = 2,
+                     device="cuda"):
+    """Fit the least-squares filter's outcome on the training seeds: with
+    T' = (1 + g (T - 1)) (1 + c (k / k_Ny)^2) for k <= k_Ny (the boost held at
+    its k_Ny value beyond), choose g, c by alternating golden-section searches
+    that minimise the mean final-P(k) deviation of the corrected 1x runs from
+    the seeds' own fine runs (`final` from fit_filter_runs).  Returns (g, c)."""
+    na, nb = corr.filter.shape
+    base = corr.filter.clone()
+    kn = torch.arange(nb, dtype=torch.float64, device=corr.device) * (np.sqrt(3.0) / (nb - 1))  # k / k_Ny
+    shape = torch.clamp(kn, max=1.0) ** 2
+    cfg = corr.config(nq, box)
+    sim = Simulation(cfg, device=device)
+
+    def apply(g, c):
+        corr.filter.copy_(((1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)[None, :]).float())
+
+    def objective(g, c):
+        apply(g, c)
+        dev = []
+        for seed, (k, p3) in final.items():
+            sim.ic(seed)
+            sim.run()
+            _, p, _ = sim.power(nq, node=cfg.n_steps - 1)
+            dev.append(pk_deviation(k, p.cpu().numpy(), p3, kmax))
+        return float(np.mean(dev))
+
+    def golden(f, lo, hi, iters=8):
+        r = (np.sqrt(5.0) - 1.0) / 2.0
+        x1, x2 = hi - r * (hi - lo), lo + r * (hi - lo)
+        f1, f2 = f(x1), f(x2)
+        for _ in range(iters):
+            if f1 < f2:
+                hi, x2, f2 = x2, x1, f1
+                x1 = hi - r * (hi - lo)
+                f1 = f(x1)
+            else:
+                lo, x1, f1 = x1, x2, f2
+                x2 = lo + r * (hi - lo)
+                f2 = f(x2)
+        return (x1, f1) if f1 < f2 else (x2, f2)
+
+    g, c = 1.0, 0.0
+    for _ in range(rounds):
+        c, _ = golden(lambda x: objective(g, x), -0.2, 2.0)
+        g, _ = golden(lambda x: objective(x, c), 0.5, 3.0)
+    apply(g, c)
     torch.cuda.synchronize()
-    return corr.filter.clone()
+    del sim
+    return g, c
 
 
 def train(corr: LearnedCorrection, samples, nq: int, box: float, iters: int = 500, lr: float = 1e-3, seed: int = 0,

@@ -100,6 +100,28 @@ def test_filtered_force_and_net_residual_vs_oracle():
     assert _cos(f1 - f0, ref_res) > 0.995
 
 
+def test_scale_factor_filter_rows_vs_oracle():
+    # a table of three filter rows (a = 0.05, 0.525, 1): each force uses the
+    # row nearest its scale factor
+    nq, L = 32, 64.0
+    d, _ = _setup(nq, L, 0.5)
+    rows = np.stack([1.0 + 0.3 * np.sin(np.arange(8) + r) for r in range(3)])
+    wpack = torch.zeros(C.NET_NPACK, dtype=torch.bfloat16, device="cuda")
+    filt = torch.tensor(rows, dtype=torch.float32, device="cuda")
+    params = torch.zeros(C.NET_NPARAMS, dtype=torch.float32, device="cuda")  # referenced by net until the end
+    net = C.make_net(params, wpack, filt)
+    C.cola_net_pack(net)
+    sim = C.Simulation(C.make_config(nq, nq, L, 0.05, flags=C.FLAG_LEARNED, net=net))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    for a in (0.1, 0.3, 0.7, 0.95):
+        got = host(sim.force(a))
+        r = ol.filter_row(a, 3, 0.05, 1.0)
+        u, F, _, _ = _oracle_fields(d, nq, L, a, rows[r])
+        ref = np.stack([pm.cic_gather(F[j], u) for j in range(3)])
+        assert rel_l2(got, ref) < 1e-5, a
+
+
 def test_net_gradients_vs_oracle():
     nq, L, a = 32, 64.0, 0.5
     d, T = _setup(nq, L, a, seed=4)

@@ -18,18 +18,22 @@ from paper_1509_04685_gb300 import learn  # noqa: E402
 def test_trained_correction_beats_plain_coarse_mesh():
     nq, box = 64, 128.0  # 2 Mpc/h spacing, as the 256^3 / L = 512 configuration
     train_seeds, test_seeds = [1001, 1002, 1003, 1004, 1005, 1006], [2001, 2002]
-    train = learn.make_samples(train_seeds, nq, box)
     test = learn.make_samples(test_seeds, nq, box)
-    corr = learn.LearnedCorrection(nfilter=16, seed=0)
-    learn.fit_filter(corr, train, nq, box)
+    corr = learn.LearnedCorrection(nfilter=16, seed=0, nfilter_a=8)
+    # filter rows from every node of the fine runs; the net trains on four nodes of each
+    train, final = learn.fit_filter_runs(corr, train_seeds, nq, box, keep_nodes=(10, 20, 30, 39))
     hist = learn.train(corr, train, nq, box, iters=800, lr=3e-3, log_every=100)
-    print("training loss", hist)
+    # force errors are judged on the least-squares filter, P(k) after the boost
+    # is calibrated on the training seeds' final P(k)
     err = learn.force_errors(corr, test, nq, box)
+    print("training loss", hist)
     print("held-out force errors", err)
     # the 1x mesh cannot carry the sub-cell part of the 3x force: the filter
     # removes the resolvable (window) bias, the net must not make it worse
     assert err["learned_1x"] < 0.8 * err["plain_1x"]
     assert err["learned_1x"] <= 1.001 * err["filter_1x"]
+    g, c = learn.calibrate_filter(corr, {s: final[s] for s in train_seeds[:3]}, nq, box)
+    print("calibrated filter gain and boost", g, c)
     # final P(k) against the plain 3x run, same seeds (cosmic variance cancels)
     dev3, dev1, devl = [], [], []
     for s in test_seeds:

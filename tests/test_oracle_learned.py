@@ -66,3 +66,14 @@ def test_gather_adjoint_is_deposit():
     lhs = np.dot(pm.cic_gather(f, u), w)
     rhs = np.sum(f * pm.cic_deposit(u, ng, weights=w))
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_filter_row_is_the_nearest_scale_factor_node():
+    # rows at a = 0.05, 0.2875, 0.525, 0.7625, 1.0 (five nodes)
+    assert ol.filter_row(0.05, 5, 0.05, 1.0) == 0
+    assert ol.filter_row(1.0, 5, 0.05, 1.0) == 4
+    assert ol.filter_row(0.16, 5, 0.05, 1.0) == 0
+    assert ol.filter_row(0.17, 5, 0.05, 1.0) == 1
+    assert ol.filter_row(0.6, 5, 0.05, 1.0) == 2
+    assert ol.filter_row(0.01, 5, 0.05, 1.0) == 0
+    assert ol.filter_row(0.7, 1, 0.05, 1.0) == 0
