@@ -272,6 +272,29 @@ def test_full_run_small_config_vs_oracle(plin, growth):
     assert np.max(np.abs(p[sel] / pr[sel] - 1)) <= 1e-3
 
 
+def test_pm_only_run_vs_oracle(plin, growth):
+    """App. B's PM-only mode (the same loop without the LPT frame): the state
+    starts at the 2LPT displacement and momentum; 32^3 on 96^3, 40 steps."""
+    nq, ng, L = 32, 96, 128.0
+    sim = C.Simulation(config(nq, ng, L, flags=C.FLAG_PM_ONLY))
+    sim.ic(seed=1)
+    ref = _oracle_state(1, nq, L, plin, growth)
+    c1, c2 = cm.lpt_momentum_coeffs(0.05, COSMO, growth)
+    ref["v"] = c1 * ref["psi1"] + c2 * ref["psi2"]
+    assert rel_l2(host(sim.v), ref["v"]) < 1e-5
+    sim.run()
+    assert sim.status() == 0
+    tab = cm.step_table(COSMO, cm.time_nodes(0.05, 1.0, 40), growth)
+    ocola.run(ref, tab, nq, ng, L, pm_only=True)
+    dq = L / nq
+    rms = np.sqrt(np.mean(np.sum((host(sim.d) - ref["d"]) ** 2, axis=0)))
+    assert rms <= 1e-3 * dq
+    k, p, n = (host(x) for x in sim.power(ng, node=39))
+    kr, pr, nr = power.power_spectrum(ref["d"], nq, ng, L)
+    sel = kr <= np.pi * ng / L / 2
+    assert np.max(np.abs(p[sel] / pr[sel] - 1)) <= 1e-3
+
+
 def test_nonfinite_input_sets_status():
     nq, ng, L = 8, 24, 32.0
     sim = C.Simulation(config(nq, ng, L))
