@@ -17,20 +17,53 @@ namespace cola {
 // l LSTR + spad(i) ES; LF: butterflies run over the lines first (consecutive
 // threads take adjacent lines; NL a power of two), else along a line.  TWM is
 // the twiddle table's stride: the table holds N TWM entries exp(-2 pi i q / (N TWM)).
-template <int NL_, bool LF_, int LSTR_, int ES_, int TWM_>
+// TWO: the passes read a pass-ordered twiddle table (see ordered_twiddles)
+// instead of that table: with butterflies along a line, neighbouring threads
+// have consecutive k, and W^{r k} read at stride r k N / (LS R) would hit the
+// same shared-memory banks.
+template <int NL_, bool LF_, int LSTR_, int ES_, int TWM_, bool TWO_ = false>
 struct TileGeo {
     static constexpr int NL = NL_;
     static constexpr bool LF = LF_;
     static constexpr int LSTR = LSTR_;
     static constexpr int ES = ES_;
     static constexpr int TWM = TWM_;
+    static constexpr bool TWO = TWO_;
 };
 // B interleaved columns (strided y/x passes)
 template <int B>
 using ColTile = TileGeo<B, true, 1, B, 1>;
 // NR rows of the half-length complex transform of real rows of 2M values (z passes)
 template <int M, int NR>
-using RowTile = TileGeo<NR, false, spad(M) + 1, 1, 2>;
+using RowTile = TileGeo<NR, false, spad(M) + 1, 1, 2, true>;
+
+// Pass-ordered twiddles: pass s (LS = product of the earlier radices, radix R)
+// reads W_{LS R}^{r k} at offset tw_offset(P, s) + (r - 1) LS + k, so that
+// consecutive k are consecutive entries.
+__host__ __device__ constexpr int tw_offset(const StaticPlan& p, int s) {
+    int off = 0, ls = p.r[0];
+    for (int q = 1; q < s; ++q) {
+        off += (p.r[q] - 1) * ls;
+        ls *= p.r[q];
+    }
+    return off;
+}
+// Fill the pass-ordered table of an N-point plan in shared memory from the
+// table tw of N TWM entries exp(-2 pi i q / (N TWM)) (the same values).
+template <int N, int T, int TWM>
+__device__ __forceinline__ void ordered_twiddles(float2* out, const float2* __restrict__ tw) {
+    constexpr StaticPlan P = static_plan(N);
+    int ls = P.r[0], off = 0;
+    for (int s = 1; s < P.nr; ++s) {
+        const int R = P.r[s], tws = N / (ls * R) * TWM;
+        for (int q = threadIdx.x; q < (R - 1) * ls; q += T) {
+            const int r = q / ls + 1, k = q - (r - 1) * ls;
+            out[off + q] = __ldg(tw + r * k * tws);
+        }
+        off += (R - 1) * ls;
+        ls *= R;
+    }
+}
 
 template <class Geo>
 struct SSmem {
@@ -91,7 +124,7 @@ __device__ __forceinline__ void spass(const In& in, const Out& out, const float2
             const int step = k * TWS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * step];
+                float2 w = Geo::TWO ? tw[(r - 1) * LS + k] : tw[r * step];
                 if (SIGN > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -107,11 +140,12 @@ __device__ __forceinline__ void srun_tail(float2* a, float2* b, const Out& out, 
     constexpr StaticPlan P = static_plan(N);
     constexpr int R = P.r[S];
     constexpr int LS = plan_ls(P, S);
+    const float2* twp = Geo::TWO ? tw + tw_offset(P, S) : tw;
     if constexpr (S == P.nr - 1) {
-        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
+        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, twp);
         __syncthreads();
     } else {
-        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{b}, tw);
+        spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{b}, twp);
         __syncthreads();
         srun_tail<N, T, Geo, SIGN, S + 1>(b, a, out, tw);
     }
@@ -192,7 +226,7 @@ __device__ __forceinline__ void spass_ip(const In& in, const Out& out, const flo
             const int step = k * TWS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * step];
+                float2 w = Geo::TWO ? tw[(r - 1) * LS + k] : tw[r * step];
                 if (SIGN > 0) w.y = -w.y;
                 v[it][r] = cmul(v[it][r], w);
             }
@@ -209,6 +243,7 @@ __device__ __forceinline__ void sip_tail(float2* a, const Out& out, const float2
     constexpr StaticPlan P = PL::P;
     constexpr int R = P.r[S];
     constexpr int LS = plan_ls(P, S);
+    static_assert(!Geo::TWO, "pass-ordered twiddles are laid out for the default plan");
     if constexpr (S == P.nr - 1) {
         if constexpr (LAST_IP)
             spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
@@ -611,7 +646,7 @@ inline int run_x_green(float2* F, int nct, int ntiles, const float2* tw, float g
 template <int M, int SP>
 struct C2rStage {
     const float2* stg;
-    const float2* tw;  // exp(-2 pi i q / 2M)
+    const float2* __restrict__ tw;  // global table exp(-2 pi i q / 2M), read through L1
     template <int R, int D>
     __device__ __forceinline__ void load(int l, int i0, float2* v) const {
         const float2* x = stg + l * SP;
@@ -624,7 +659,7 @@ struct C2rStage {
                 bb.y = 0.f;
             }
             const float2 b = cconj(bb);
-            float2 w = tw[k];
+            float2 w = __ldg(tw + k);
             w.y = -w.y;
             const float2 d = cmul(csub(a, b), w);
             v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
@@ -663,13 +698,16 @@ struct FixStage {
     }
 };
 
+// entries of the pass-ordered twiddle table of an M-point plan
+constexpr int ordered_tw_size(int M) { return tw_offset(static_plan(M), static_plan(M).nr); }
+
 template <int N, int NR, int T>
 constexpr size_t z_c2r_smem() {
-    return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + N) * 8;
+    return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2)) * 8;
 }
 template <int N, int NR, int T>
 constexpr size_t z_r2c_smem() {
-    return ((size_t)NR * N + 2 * (size_t)NR * (spad(N / 2) + 1) + N) * 8;
+    return ((size_t)NR * N + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2)) * 8;
 }
 
 // inverse c2r along z, in place on rows of rs complex (the runtime form is
@@ -687,8 +725,8 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long r
     float2* stg = sm;
     float2* A = stg + NR * SP;
     float2* Bf = A + NR * Geo::LSTR;
-    float2* tws = Bf + NR * Geo::LSTR;
-    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    float2* tws = Bf + NR * Geo::LSTR;  // pass-ordered twiddles of the M-point transform
+    ordered_twiddles<M, T, 2>(tws, tw);
     auto prefetch = [&](int t) {
         const long long row0 = (long long)t * NR;
 #pragma unroll 4
@@ -707,7 +745,7 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long r
         auto next = [&]() {
             if (tn < ntiles) prefetch(tn);
         };
-        srun_out<M, T, Geo, +1>(C2rStage<M, SP>{stg, tws}, SRowStore{data, rs, (long long)t * NR, nrows}, A, Bf, tws,
+        srun_out<M, T, Geo, +1>(C2rStage<M, SP>{stg, tw}, SRowStore{data, rs, (long long)t * NR, nrows}, A, Bf, tws,
                                 next);
     }
 }
@@ -727,8 +765,8 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_r2c_fix_s(unsigned long long* _
     unsigned long long* stg = reinterpret_cast<unsigned long long*>(sm);
     float2* A = sm + NR * N;
     float2* Bf = A + NR * Geo::LSTR;
-    float2* tws = Bf + NR * Geo::LSTR;
-    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    float2* tws = Bf + NR * Geo::LSTR;  // pass-ordered twiddles of the M-point transform
+    ordered_twiddles<M, T, 2>(tws, tw);
     auto prefetch = [&](int t) {
         const long long row0 = (long long)t * NR;
 #pragma unroll 4
@@ -771,7 +809,7 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_r2c_fix_s(unsigned long long* _
             const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
             const float2 D = csub(a, b);
             const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-            __stcs(out + obase[l] + k, cadd(E, cmul(tws[k], O)));
+            __stcs(out + obase[l] + k, cadd(E, cmul(__ldg(tw + k), O)));
         }
     }
 }
