@@ -707,7 +707,7 @@ constexpr size_t z_c2r_smem() {
 }
 template <int N, int NR, int T>
 constexpr size_t z_r2c_smem() {
-    return ((size_t)NR * N + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2)) * 8;
+    return ((size_t)NR * N + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2) + N / 2 + 1) * 8;
 }
 
 // inverse c2r along z, in place on rows of rs complex (the runtime form is
@@ -766,7 +766,9 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_r2c_fix_s(unsigned long long* _
     float2* A = sm + NR * N;
     float2* Bf = A + NR * Geo::LSTR;
     float2* tws = Bf + NR * Geo::LSTR;  // pass-ordered twiddles of the M-point transform
+    float2* twh = tws + ordered_tw_size(M);  // W_N^k, k <= M, for the r2c post-processing
     ordered_twiddles<M, T, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += T) twh[q] = __ldg(tw + q);
     auto prefetch = [&](int t) {
         const long long row0 = (long long)t * NR;
 #pragma unroll 4
@@ -809,7 +811,7 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_r2c_fix_s(unsigned long long* _
             const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
             const float2 D = csub(a, b);
             const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-            __stcs(out + obase[l] + k, cadd(E, cmul(__ldg(tw + k), O)));
+            __stcs(out + obase[l] + k, cadd(E, cmul(twh[k], O)));
         }
     }
 }
