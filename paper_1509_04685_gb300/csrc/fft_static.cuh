@@ -646,7 +646,7 @@ inline int run_x_green(float2* F, int nct, int ntiles, const float2* tw, float g
 template <int M, int SP>
 struct C2rStage {
     const float2* stg;
-    const float2* __restrict__ tw;  // global table exp(-2 pi i q / 2M), read through L1
+    const float2* tw;  // W_2M^k = exp(-2 pi i k / 2M) for k <= M (shared memory)
     template <int R, int D>
     __device__ __forceinline__ void load(int l, int i0, float2* v) const {
         const float2* x = stg + l * SP;
@@ -659,7 +659,7 @@ struct C2rStage {
                 bb.y = 0.f;
             }
             const float2 b = cconj(bb);
-            float2 w = __ldg(tw + k);
+            float2 w = tw[k];
             w.y = -w.y;
             const float2 d = cmul(csub(a, b), w);
             v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
@@ -703,7 +703,7 @@ constexpr int ordered_tw_size(int M) { return tw_offset(static_plan(M), static_p
 
 template <int N, int NR, int T>
 constexpr size_t z_c2r_smem() {
-    return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2)) * 8;
+    return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2) + N / 2 + 1) * 8;
 }
 template <int N, int NR, int T>
 constexpr size_t z_r2c_smem() {
@@ -726,7 +726,9 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long r
     float2* A = stg + NR * SP;
     float2* Bf = A + NR * Geo::LSTR;
     float2* tws = Bf + NR * Geo::LSTR;  // pass-ordered twiddles of the M-point transform
+    float2* twh = tws + ordered_tw_size(M);  // W_N^k, k <= M, for the c2r pre-processing
     ordered_twiddles<M, T, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += T) twh[q] = __ldg(tw + q);
     auto prefetch = [&](int t) {
         const long long row0 = (long long)t * NR;
 #pragma unroll 4
@@ -745,7 +747,7 @@ __global__ void __launch_bounds__(T, MB) k_fft_z_c2r_s(float2* data, long long r
         auto next = [&]() {
             if (tn < ntiles) prefetch(tn);
         };
-        srun_out<M, T, Geo, +1>(C2rStage<M, SP>{stg, tw}, SRowStore{data, rs, (long long)t * NR, nrows}, A, Bf, tws,
+        srun_out<M, T, Geo, +1>(C2rStage<M, SP>{stg, twh}, SRowStore{data, rs, (long long)t * NR, nrows}, A, Bf, tws,
                                 next);
     }
 }
