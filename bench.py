@@ -227,8 +227,10 @@ def algorithmic_bytes(name: str, nq: int, ng: int) -> float:
         "deposit": 12.0 * Np + F,
         "fft_z_r2c_fix": 2 * F + Mc,
         "fft_y_fwd": 2 * Mc, "fft_x_fwd": 2 * Mc, "fft_x_inv": 2 * Mc,
-        "fft_y_inv": 6 * Mc,          # all three force components in one launch
-        "fft_x_green": 4 * Mc,
+        # the fused x pass writes F_x and Psi = IFFT_x(phi); the y inverse reads both and
+        # writes F_x, F_y = IFFT_y(i k_y Psi) and F_z = i k_z IFFT_y(Psi)
+        "fft_y_inv": 5 * Mc,
+        "fft_x_green": 3 * Mc,
         "fft_z_c2r": 3 * (Mc + M),    # all three force components in one launch
         "gather_kick_drift": 72.0 * Np + 3 * M,
     }.get(name, 0.0)

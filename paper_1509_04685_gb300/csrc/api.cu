@@ -113,11 +113,12 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * XB * P, ng, (int)XB, 3 * XB * ng * P, 3 * P}, kKYFwd)))
         return rc;
     const double kmax = std::sqrt(3.0) * 3.14159265358979323846 * ng / cfg->box;
-    if ((rc = fft_x_green(F, ng, (float)(green / ng3), (float)(2.0 * 3.14159265358979323846 / cfg->box), tw, s, filt,
-                          nfilt, nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f)))
+    const float kf = (float)(2.0 * 3.14159265358979323846 / cfg->box);
+    bool psi = false;
+    if ((rc = fft_x_green(F, ng, (float)(green / ng3), kf, tw, s, filt, nfilt,
+                          nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f, &psi)))
         return rc;
-    if ((rc = fft_lines(F, ng, +1, tw, s, LineGeom{3 * XB * P, 3 * ng, (int)(3 * XB), 3 * XB * ng * P, P}, kKYInv)))
-        return rc;
+    if ((rc = fft_y_inverse_force(F, ng, tw, s, psi, kf))) return rc;
     if ((rc = fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2))) return rc;
     if (learned) return net_forward(cfg->net, wsp(ws, L.lrn), ng, nq, (float)green, F, s);
     return COLA_OK;

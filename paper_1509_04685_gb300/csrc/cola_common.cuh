@@ -514,6 +514,7 @@ enum KernelId {
     kKDeposit = 0, kKZr2cFix, kKZr2c, kKYFwd, kKXFwd, kKXGreen, kKYInv, kKXInv, kKZc2r, kKGatherKD, kKGather,
     kKFixToDelta, kKPkShells, kKPkReduce, kKIc, kKSetup, kKLearned, kNumKernelIds
 };
+// a ProfScope with id < 0 records nothing (launches inside an enclosing scope)
 class ProfScope {
   public:
     ProfScope(int id, cudaStream_t s);
@@ -550,7 +551,11 @@ int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaS
 // interleaved force mesh (rows (ix, iy, c)): delta_k in c = 0 -> F_x, F_y, F_z in c = 0, 1, 2
 // filt: optional radial transfer function T(|k|) on nodes b * fstep, b < nfilt (nullptr: none)
 int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s,
-                const float* filt = nullptr, int nfilt = 0, float fstep = 1.f);
+                const float* filt = nullptr, int nfilt = 0, float fstep = 1.f, bool* psi = nullptr);
+// inverse y pass of the force mesh after fft_x_green: three component lines, or,
+// if the x pass left Psi in component 1 (psi), F_y = IFFT_y(i k_y Psi) and
+// F_z = i k_z IFFT_y(Psi) from it (kf = 2 pi / L)
+int fft_y_inverse_force(float2* F, int n, const float2* tw, cudaStream_t s, bool psi, float kf);
 __host__ __device__ __forceinline__ FRow force_rows(int ng) { return FRow{ng, xblock_shift(ng), 3}; }
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,

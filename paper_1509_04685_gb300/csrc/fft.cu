@@ -574,7 +574,8 @@ int fft_strided(float2* data, int n, int axis, int sign, const float2* tw, cudaS
 }
 
 int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cudaStream_t s, const float* filt,
-                int nfilt, float fstep) {
+                int nfilt, float fstep, bool* psi) {
+    if (psi) *psi = false;
     FftPlan plan;
     if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
     const long long P = fft_pitch(n);
@@ -584,7 +585,10 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     int rc = COLA_OK;
     {
         const int nct = (n / 2 + 1 + B - 1) / B;
-        if (launch_x_green_static(F, n, B, nct, n * nct, tw, gscale, kf, filt, nfilt, fstep, s, &rc)) return rc;
+        if (launch_x_green_static(F, n, B, nct, n * nct, tw, gscale, kf, filt, nfilt, fstep, s, &rc)) {
+            if (psi) *psi = true;  // the specialised passes leave Psi in component 1
+            return rc;
+        }
     }
     while (B > 2 && (n * B > 512 * kGreenEpt || !runtime_tile_fits(n, B))) B /= 2;
     const int nct = (n / 2 + 1 + B - 1) / B;
@@ -601,6 +605,50 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
     k_fft_x_green<<<persistent_grid(smem, ntiles), T, smem, s>>>(F, F, F + P, F + 2 * P, n, 3ll * XB * P, xl, B, nct,
                                                                   ntiles, plan, tw, gscale, kf, filt, nfilt, fstep);
     return check_launch();
+}
+
+// F_y = i k_y Psi and F_z = i k_z Psi from Psi in component 1, for tile widths
+// without a specialised Psi y pass
+__global__ void k_expand_psi(float2* F, int n, int P, int xbs, float kf) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n2 = (long long)n * n;
+    if (e >= n2 * (n / 2 + 1)) return;
+    const int kz = (int)(e % (n / 2 + 1));
+    const long long r = e / (n / 2 + 1);
+    const int x = (int)(r / n), y = (int)(r - (long long)x * n);
+    const FRow fr{n, xbs, 3};
+    float2* f1 = F + frow(x, y, 1, fr) * P + kz;
+    float2* f2 = F + frow(x, y, 2, fr) * P + kz;
+    const float ky = (y == n / 2) ? 0.f : kf * (float)(y < n / 2 ? y : y - n);
+    const float kzf = (kz == n / 2) ? 0.f : kf * (float)kz;
+    const float2 v = *f1;
+    *f1 = make_float2(-ky * v.y, ky * v.x);
+    *f2 = make_float2(-kzf * v.y, kzf * v.x);
+}
+
+int fft_y_inverse_force(float2* F, int n, const float2* tw, cudaStream_t s, bool psi, float kf) {
+    ProfScope ps(kKYInv, s);
+    const long long P = fft_pitch(n);
+    const FRow fr = force_rows(n);
+    const long long XB = 1ll << fr.xbs;
+    const LineGeom all3{3 * XB * P, 3 * n, (int)(3 * XB), 3 * XB * n * P, P};
+    if (!psi) return fft_lines(F, n, +1, tw, s, all3, -1);
+    FftPlan plan;
+    if (!make_plan(n, &plan)) return COLA_EUNSUPPORTED_SIZE;
+    const int B = strided_cols(n);
+    const int nct = (n / 2 + 1 + B - 1) / B;
+    // lines of one component: outer x = xb XB + xi
+    const LineGeom one{3 * XB * P, n, (int)XB, 3 * XB * n * P, 3 * P};
+    int rc = COLA_OK;
+    if ((long long)n * nct <= 0x7fffffff &&
+        launch_y_psi_static(F + P, n, B, one, P, nct, n * nct, tw, kf, s, &rc)) {
+        if (rc) return rc;
+        return fft_lines(F, n, +1, tw, s, one, -1);
+    }
+    const long long ne = (long long)n * n * (n / 2 + 1);
+    k_expand_psi<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(F, n, (int)P, fr.xbs, kf);
+    if ((rc = check_launch())) return rc;
+    return fft_lines(F, n, +1, tw, s, all3, -1);
 }
 
 }  // namespace cola

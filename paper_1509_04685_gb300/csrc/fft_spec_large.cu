@@ -115,4 +115,17 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
 }
 
 
+
+bool launch_y_psi_static(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
+                         const float2* tw, float kf, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, BB, TT)                                                   \
+    if (n == NN && B == BB) {                                                   \
+        *rc = run_y_psi<NN, BB, TT>(data, lg, comp2, nct, ntiles, tw, kf, s); \
+        return true;                                                            \
+    }
+    COLA_STRIDED_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return launch_y_psi_static_small(data, n, B, lg, comp2, nct, ntiles, tw, kf, s, rc);
+}
+
 }  // namespace cola

@@ -61,4 +61,17 @@ bool launch_x_green_static_small(float2* F, int n, int B, int nct, int ntiles, c
 // the small meshes run the fused pass at the strided passes' width
 int launch_static_green_tile_small(int) { return 0; }
 
+
+bool launch_y_psi_static_small(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
+                         const float2* tw, float kf, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, BB, TT)                                                   \
+    if (n == NN && B == BB) {                                                   \
+        *rc = run_y_psi<NN, BB, TT>(data, lg, comp2, nct, ntiles, tw, kf, s); \
+        return true;                                                            \
+    }
+    COLA_STRIDED_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return false;
+}
+
 }  // namespace cola

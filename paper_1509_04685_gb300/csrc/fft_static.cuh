@@ -342,38 +342,9 @@ struct SXIO {
     }
 };
 
-// Psi = IFFT_x(phi) written as F_y = i k_y Psi and F_z = i k_z Psi (both
-// constant along an x line)
-template <int N>
-struct SYZStore {
-    float2* fy;
-    float2* fz;
-    float ky, kf;
-    int col0;
-    template <int R, int D>
-    __device__ __forceinline__ void store(int l, int i0, const float2* v) const {
-        using G = XGeom<N>;
-        const float kz = (col0 + l == N / 2) ? 0.f : kf * (float)(col0 + l);
-        if constexpr (D % G::XB == 0) {
-            const long long q0 = G::off(i0) + l;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const long long q = q0 + (long long)r * (D / G::XB) * G::SB;
-                __stcs(fy + q, make_float2(-ky * v[r].y, ky * v[r].x));
-                __stcs(fz + q, make_float2(-kz * v[r].y, kz * v[r].x));
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const long long q = G::off(i0 + r * D) + l;
-                __stcs(fy + q, make_float2(-ky * v[r].y, ky * v[r].x));
-                __stcs(fz + q, make_float2(-kz * v[r].y, kz * v[r].x));
-            }
-        }
-    }
-};
-
-// i k_x times a spectrum tile read from shared memory (x component of the force)
+// i k times a spectrum tile read from shared memory, k the wave number of the
+// line index (0 on the Nyquist index): the x component of the force in the x
+// pass (i k_x phi), the y component in the y pass (i k_y Psi)
 template <int N, class Geo>
 struct IkxLoad {
     float2* p;
@@ -517,9 +488,8 @@ __global__ void __launch_bounds__(T, 1) k_fft_x_green_s(float2* F, int nct, int 
                                                                          tws, NoHook{});
         const int tn = t + gridDim.x;
         if (tn < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(tn), xo);
-        const float ky_eff = (iy == half) ? 0.f : ky;
-        sip_run<N, T, Geo, +1, true, false, typename GreenPlans<N>::I2>(SSmem<Geo>{A}, SYZStore<N>{F + off + G::P, F + off + 2 * G::P, ky_eff, kf, col0},
-                                            A, tws, NoHook{});
+        sip_run<N, T, Geo, +1, true, false, typename GreenPlans<N>::I2>(SSmem<Geo>{A}, SXIO<N>{F + off + G::P}, A,
+                                                                        tws, NoHook{});
     }
 }
 
@@ -589,7 +559,6 @@ __global__ void __launch_bounds__(T, 1) k_fft_x_green3_s(float2* F, int nct, int
             phi[q] = cscale(elem(X, q), gk);
         }
         __syncthreads();
-        const float ky_eff = (iy == half) ? 0.f : ky;
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             const int i = i0 + q * TB;
@@ -601,9 +570,74 @@ __global__ void __launch_bounds__(T, 1) k_fft_x_green3_s(float2* F, int nct, int
 #pragma unroll
         for (int q = 0; q < EPT; ++q) elem(A, q) = phi[q];
         __syncthreads();
-        srun_out<N, T, ColTile<B>, +1>(SSmem<ColTile<B>>{A}, SYZStore<N>{F + off + G::P, F + off + 2 * G::P, ky_eff, kf, col0}, W, A,
-                              tws, NoHook{});
+        srun_out<N, T, ColTile<B>, +1>(SSmem<ColTile<B>>{A}, SXIO<N>{F + off + G::P}, W, A, tws, NoHook{});
     }
+}
+
+// global column tile written as i k_z times the values, k_z the wave number of
+// the tile's column (0 on the Nyquist column n/2)
+struct SColIkz {
+    float2* g;
+    long long S;
+    float kf;
+    int col0, half;
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l, int i0, const float2* v) const {
+        const float kz = (col0 + l == half) ? 0.f : kf * (float)(col0 + l);
+        float2* q = g + (long long)i0 * S + l;
+        const long long st = (long long)D * S;
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(q + r * st, make_float2(-kz * v[r].y, kz * v[r].x));
+    }
+};
+
+// Inverse y pass of the force mesh's second component, which the fused x pass
+// leaves as Psi = IFFT_x(phi) (the x transform of the potential): one staged
+// tile of Psi gives F_y = IFFT_y(i k_y Psi) (k_y varies along the y line) into
+// component 1 and F_z = i k_z IFFT_y(Psi) (k_z is the column's, constant along
+// the line) into component 2.  lg addresses component 1; component 2 follows
+// at + comp2.
+template <int N, int B, int T>
+__global__ void __launch_bounds__(T, 1) k_fft_y_psi_s(float2* data, LineGeom lg, long long comp2, int nct, int ntiles,
+                                                       const float2* __restrict__ tw, float kf) {
+    using Geo = ColTile<B>;
+    constexpr int TSZ = spad(N) * B;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = sm + TSZ;
+    float2* tws = A + TSZ;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    const SCol rows{nullptr, lg.S};
+    auto tile_base = [&](int t) {
+        const int o = t / nct;
+        const int ct = t - o * nct;
+        const int o1 = o / lg.o2n, o2 = o - o1 * lg.o2n;
+        return data + o1 * lg.s1 + o2 * lg.s2 + ct * B;
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) stile_prefetch<N, B, T>(stg, tile_base(t), rows);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        float2* base = tile_base(t);
+        const int col0 = (t - (t / nct) * nct) * B;
+        sip_run<N, T, Geo, +1, false, false>(IkxLoad<N, Geo>{stg, kf}, SCol{base, lg.S}, A, tws, NoHook{});
+        const int tn = t + gridDim.x;
+        auto next = [&]() {
+            if (tn < ntiles) stile_prefetch<N, B, T>(stg, tile_base(tn), rows);
+        };
+        sip_run<N, T, Geo, +1, false, false>(SSmem<Geo>{stg}, SColIkz{base + comp2, lg.S, kf, col0, N / 2}, A, tws,
+                                             next);
+    }
+}
+
+template <int N, int B, int T>
+inline int run_y_psi(float2* data, LineGeom lg, long long comp2, int nct, int ntiles, const float2* tw, float kf,
+                     cudaStream_t s) {
+    const size_t smem = ((size_t)2 * spad(N) * B + N) * 8;
+    if (!set_smem((const void*)k_fft_y_psi_s<N, B, T>, smem)) return COLA_ECUDA;
+    k_fft_y_psi_s<N, B, T><<<persistent_grid(smem, ntiles), T, smem, s>>>(data, lg, comp2, nct, ntiles, tw, kf);
+    return check_launch();
 }
 
 template <int N, int B, int T>
@@ -865,6 +899,12 @@ bool static_tile_ok(int n, int B);
 // strided passes' width)
 int static_green_tile(int n);
 int launch_static_green_tile_small(int n);
+// inverse y pass of the Psi component (k_fft_y_psi_s) for (n, B); false when
+// there is no specialisation, without launching
+bool launch_y_psi_static(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
+                         const float2* tw, float kf, cudaStream_t s, int* rc);
+bool launch_y_psi_static_small(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
+                               const float2* tw, float kf, cudaStream_t s, int* rc);
 // the mesh sizes below 512 (batched ensembles, tests), in fft_spec_small.cu
 bool launch_strided_static_small(float2* data, int n, int B, int sign, LineGeom lg, int nct, int ntiles,
                                  const float2* tw, cudaStream_t s, int* rc);

@@ -21,7 +21,7 @@ const char* kNames[kNumKernelIds] = {"deposit",     "fft_z_r2c_fix", "fft_z_r2c"
 }  // namespace
 
 ProfScope::ProfScope(int id, cudaStream_t s) : rec_(-1), s_(s) {
-    if (!g_on || g_used >= g_recs.size()) return;
+    if (!g_on || id < 0 || g_used >= g_recs.size()) return;
     rec_ = (int)g_used++;
     g_recs[rec_].id = id;
     cudaEventRecord(g_recs[rec_].start, s);
