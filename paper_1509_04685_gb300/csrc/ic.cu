@@ -33,25 +33,33 @@ __device__ double E_of(double a, const CosmoD& c) {
     return sqrt(c.om / (a * a * a) + c.ok / (a * a) + c.ol);
 }
 
+// Growth ODEs in y = ln a for D1 = a u and D2 = a^2 w (Sec. 2.2's 2LPT growth
+// factors; the same equations as D1'' + (2 + dlnE/dy) D1' = 3/2 Om(a) D1 and
+// D2'' + (2 + dlnE/dy) D2' = 3/2 Om(a) (D2 - D1^2)): u and w are constant in the
+// matter era, so RK4 in these variables is accurate with far fewer steps than
+// in D1, D2 themselves, which grow like a and a^2.  State s = (u, u', w, w',
+// K, Dr) with K = int dy / E and Dr = int dy / (a^2 E) over the current segment.
 __device__ void growth_rhs(double y, const double* s, double* ds, const CosmoD& c) {
     const double a = exp(y);
     const double a2 = a * a, a3 = a2 * a;
     const double E2 = c.om / a3 + c.ok / a2 + c.ol;
     const double E = sqrt(E2);
     const double oma = c.om / a3 / E2;
-    const double dlnE = (-3.0 * c.om / a3 - 2.0 * c.ok / a2) / (2.0 * E2);
-    const double fr = 2.0 + dlnE;
+    const double fr = 2.0 + (-3.0 * c.om / a3 - 2.0 * c.ok / a2) / (2.0 * E2);
     ds[0] = s[1];
-    ds[1] = -fr * s[1] + 1.5 * oma * s[0];
+    ds[1] = -(2.0 + fr) * s[1] - (1.0 + fr - 1.5 * oma) * s[0];
     ds[2] = s[3];
-    ds[3] = -fr * s[3] + 1.5 * oma * (s[2] - s[0] * s[0]);
+    ds[3] = -(4.0 + fr) * s[3] - (4.0 + 2.0 * fr - 1.5 * oma) * s[2] - 1.5 * oma * s[0] * s[0];
     ds[4] = 1.0 / E;
     ds[5] = 1.0 / (a2 * E);
 }
 
+// step bounds in y: from the start to the first output, and between outputs
+constexpr double kHEarly = 1.0 / 64.0;
+constexpr double kHSeg = 1.0 / 256.0;
+
 // Advance s from y0 to y1 with RK4 steps of at most hmax.
-__device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c) {
-    const double hmax = 1.0 / 512.0;
+__device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c, double hmax) {
     const double span = y1 - y0;
     if (span <= 0.0) return;
     const int nstep = (int)ceil(span / hmax);
@@ -73,11 +81,12 @@ __device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c) {
 
 constexpr double kAEarly = 1e-5;
 
+// the Einstein-de Sitter modes at a = kAEarly: D1 = a, D2 = -3/7 a^2
 __device__ void growth_init(double* s) {
-    s[0] = kAEarly;
-    s[1] = kAEarly;
-    s[2] = -3.0 / 7.0 * kAEarly * kAEarly;
-    s[3] = -6.0 / 7.0 * kAEarly * kAEarly;
+    s[0] = 1.0;
+    s[1] = 0.0;
+    s[2] = -3.0 / 7.0;
+    s[3] = 0.0;
     s[4] = s[5] = 0.0;
 }
 
@@ -97,15 +106,15 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
     for (int j = 0; j < n; ++j) {
         const double aj = node_a(j, n, ai, af, sampling, sp);
         const double yj = log(aj);
-        rk4_to(s, y, yj, c);
+        rk4_to(s, y, yj, c, j == 0 ? kHEarly : kHSeg);
         y = yj;
         double* r = tab + (size_t)j * kTableCols;
         r[0] = aj;
         r[1] = 1.5 * c.om / aj;
-        r[8] = s[0];  // raw D1 (normalised below)
-        r[9] = s[2];
-        r[10] = s[1] / aj;
-        r[11] = s[3] / aj;
+        r[8] = aj * s[0];  // raw D1 (normalised below)
+        r[9] = aj * aj * s[2];
+        r[10] = s[0] + s[1];                  // dD1/da
+        r[11] = aj * (2.0 * s[2] + s[3]);     // dD2/da
         r[4] = (j > 0) ? s[4] : 0.0;  // segment mid_{j-1} -> a_j
         double drift = (j > 0) ? s[5] : 0.0;
         if (j > 0) tab[(size_t)(j - 1) * kTableCols + 5] += drift;
@@ -113,7 +122,7 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
         if (j + 1 < n) {
             const double an = node_a(j + 1, n, ai, af, sampling, sp);
             const double ym = log(0.5 * (aj + an));
-            rk4_to(s, y, ym, c);
+            rk4_to(s, y, ym, c, kHSeg);
             y = ym;
             r[4] += s[4];  // a_j -> mid_j
             r[5] = s[5];
@@ -122,15 +131,16 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
             r[5] = 0.0;
         }
     }
-    // normalisation D1(1) = 1
-    if (y < 0.0) rk4_to(s, y, 0.0, c);
+    // normalisation D1(1) = 1 (at a = 1, D1 = u)
+    if (y < 0.0) rk4_to(s, y, 0.0, c, kHSeg);
     const double norm = (y <= 0.0) ? s[0] : 0.0;
     double nrm = norm;
     if (y > 0.0) {
         // a_final beyond 1: integrate again from the start to a = 1
         double t[6];
         growth_init(t);
-        rk4_to(t, log(kAEarly), 0.0, c);
+        rk4_to(t, log(kAEarly), log(ai), c, kHEarly);
+        rk4_to(t, log(ai), 0.0, c, kHSeg);
         nrm = t[0];
     }
     for (int j = 0; j < n; ++j) {
@@ -169,14 +179,20 @@ __global__ void k_snapshot(double* snap, double a_node, double a_out, CosmoD c, 
     const double lo = fmin(a_node, a_out), hi = fmax(a_node, a_out);
     double s[6];
     growth_init(s);
-    rk4_to(s, log(kAEarly), log(lo), c);
-    const double D1lo = s[0], D2lo = s[2];
+    rk4_to(s, log(kAEarly), log(lo), c, kHEarly);
+    const double D1lo = lo * s[0], D2lo = lo * lo * s[2];
     s[4] = s[5] = 0.0;
-    rk4_to(s, log(lo), log(hi), c);
-    const double D1hi = s[0], D2hi = s[2], dr = s[5];
     double t[6];
-    growth_init(t);
-    rk4_to(t, log(kAEarly), 0.0, c);
+    for (int q = 0; q < 6; ++q) t[q] = s[q];
+    rk4_to(s, log(lo), log(hi), c, kHSeg);
+    const double D1hi = hi * s[0], D2hi = hi * hi * s[2], dr = s[5];
+    // D1(1) for the normalisation (continue from lo; from the start if lo > 1)
+    if (lo > 1.0) {
+        growth_init(t);
+        rk4_to(t, log(kAEarly), 0.0, c, kHEarly);
+    } else {
+        rk4_to(t, log(lo), 0.0, c, kHSeg);
+    }
     const double nrm = t[0];
     const double sign = (a_out >= a_node) ? 1.0 : -1.0;
     snap[0] = sign * dr;
