@@ -244,10 +244,16 @@ def step_reference_bytes(nq: int, ng: int) -> float:
     return M + (M + Mc) + 3 * (Mc + M) + 3 * M + 84.0 * nq**3
 
 
+# sources that define and launch the kernels of a step (profiles/ncu_traffic.json
+# holds counters taken on them; a change here makes the stored traffic stale)
+STEP_SOURCES = ("cola_common.cuh", "fft_static.cuh", "fft.cu", "fft_spec_large.cu", "fft_spec_small.cu", "pm.cu",
+                "api.cu")
+
+
 def csrc_digest() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1509_04685_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in STEP_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
