@@ -40,6 +40,9 @@ WORKLOADS = {
     "ensemble": dict(name="cola_ensemble_48_seeds_96-128-160^3_pm1-2-3_40steps", nq=0, ng=0, box=0.0),
     # learned 1x mesh vs plain 3x mesh, 256^3 particles, L = 512 Mpc/h
     "learned": dict(name="cola_learned_256^3_particles_256^3_vs_768^3_mesh_L512_40steps", nq=0, ng=0, box=0.0),
+    # the largest run's learned 1.5x form vs its plain 3x form, P(k) at z = 1, 0.5, 0
+    "largest_learned": dict(name="cola_learned_768^3_particles_1152^3_vs_2304^3_mesh_L1536_40steps", nq=0, ng=0,
+                            box=0.0),
 }
 
 
@@ -195,6 +198,92 @@ def run_learned(args, rank, world, C, torch, dist):
                          "k": [round(float(x), 4) for x in k[sel]]},
             "training": {"seconds": t_train, "loss": hist, "filter_gain": gain, "filter_boost": boost,
                          "calibration_seeds": 4},
+            "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
+        }), flush=True)
+
+
+def run_largest_learned(args, rank, world, C, torch, dist):
+    """The largest run's two forms at the same seed: plain PM_grid = 3 (768^3
+    particles on 2304^3) and the learned 1.5x form (768^3 on 1152^3), L = 1536
+    Mpc/h, 40 steps, P(k) at z = 1, 0.5 and 0 on a 768^3 mesh.  The learned form
+    is the radial filter alone: the net's activations would need ~150 GB at
+    1152^3.  The filter is fitted and calibrated in a 128^3 / L = 256 box at the
+    same resolution (its nodes are fixed in k L / ng).  The value is the learned
+    form's particle-steps/s."""
+    import numpy as np
+
+    from paper_1509_04685_gb300 import learn
+
+    t0 = time.perf_counter()
+    nq_t, box_t = 128, 256.0
+    train_seeds = [1001 + 100 * rank + i for i in range(args.learned_train)]
+    corr = learn.LearnedCorrection(nfilter=16, seed=0, nfilter_a=8, mesh_factor=1.5)
+    _, final = learn.fit_filter_runs(corr, train_seeds, nq_t, box_t, outputs=(0.5, 2.0 / 3.0, 1.0))
+    gain, boost = learn.calibrate_filter(corr, {s: final[s] for s in train_seeds[:4]}, nq_t, box_t, use_net=False)
+    torch.cuda.empty_cache()
+    t_train = time.perf_counter() - t0
+
+    nq, box, ng_pk, seed = 768, 1536.0, 768, 1 + rank
+    a_nodes = A_INIT + np.arange(N_NODES) * (1.0 - A_INIT) / (N_NODES - 1)
+    outputs = [(1.0, 0.5), (0.5, 2.0 / 3.0), (0.0, 1.0)]  # (z, a)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    launches0 = C.cola_launch_count()
+
+    def run(cfg):
+        sim = C.Simulation(cfg)
+        sim.ic(seed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms, pks, j = 0.0, {}, 0
+        for z, a in outputs:
+            node = N_NODES - 1 if a >= 1.0 else int(np.floor((a - A_INIT) / (a_nodes[1] - a_nodes[0]) + 1e-9))
+            torch.cuda.synchronize()
+            e0.record()
+            sim.run(range(j, node if a < 1.0 else N_NODES))
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            j = node if a < 1.0 else N_NODES
+            k, p, _ = sim.power(ng_pk, a_out=a, node=node)
+            pks[z] = (k.cpu().numpy(), p.cpu().numpy())
+        if sim.status() != 0:
+            raise SystemExit("device status after the largest run")
+        del sim
+        torch.cuda.empty_cache()
+        return ms, pks
+
+    ms3, pk3 = run(C.make_config(nq, 3 * nq, box, A_INIT, 1.0, N_NODES))
+    msl, pkl = run(corr.config(nq, box, use_net=False))
+    clk = clocks.stop()
+    pkdev = {}
+    for z, _ in outputs:
+        k, p3 = pk3[z]
+        _, pl = pkl[z]
+        sel = k <= 1.0
+        pkdev[f"z={z:g}"] = {"max_abs_dev": float(np.max(np.abs(pl[sel] / p3[sel] - 1))),
+                             "mean_abs_dev": float(np.mean(np.abs(pl[sel] / p3[sel] - 1))),
+                             "ratio_at_k": {f"{kk:.2f}": round(float(r), 4) for kk, r in
+                                            zip(k[sel][::10], (pl[sel] / p3[sel])[::10])}}
+    ps_l = nq**3 * N_NODES / (msl * 1e-3)
+    ps_3 = nq**3 * N_NODES / (ms3 * 1e-3)
+    tot = torch.tensor([ps_l, ps_3], device="cuda")
+    if dist:
+        dist.all_reduce(tot)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "particle-steps/s of the learned 1.5x-mesh form (768^3 particles on 1152^3, L=1536 Mpc/h)",
+            "value": float(tot[0].item()), "unit": UNIT, "n_gpus": world, "steps": N_NODES, "warmup": 0,
+            "ms_per_step": msl / N_NODES, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["largest_learned"]["name"], "nq": nq, "ng_learned": 1152,
+                       "ng_plain": 3 * nq, "box": box, "n_steps": N_NODES, "seed": seed,
+                       "correction": "radial filter alone (16 k nodes x 8 scale-factor rows), fitted on "
+                                     f"{len(train_seeds)} runs of 128^3 on 192^3 vs 384^3 (L=256), calibrated on 4 "
+                                     "at z = 1, 0.5, 0",
+                       "pk_mesh": ng_pk, "parallelism": f"replicas{world}"},
+            "plain_3x": {"value": float(tot[1].item()), "ms_per_step": ms3 / N_NODES},
+            "speedup_vs_plain_3x": ps_l / ps_3,
+            "pk_vs_plain_3x_k_le_1": pkdev,
+            "training": {"seconds": t_train, "filter_gain": gain, "filter_boost": boost},
             "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
         }), flush=True)
 
@@ -402,8 +491,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    if args.workload in ("ensemble", "learned"):
-        (run_ensemble if args.workload == "ensemble" else run_learned)(args, rank, world, C, torch, dist)
+    if args.workload in ("ensemble", "learned", "largest_learned"):
+        {"ensemble": run_ensemble, "learned": run_learned,
+         "largest_learned": run_largest_learned}[args.workload](args, rank, world, C, torch, dist)
         if dist:
             dist.destroy_process_group()
         return

@@ -69,7 +69,10 @@ typedef struct cola_cosmology {
  * k_b = b sqrt(3) pi ng / (L (nfilter - 1)); NULL means T = 1).  With
  * nfilter_a > 1 the filter holds nfilter_a rows of nfilter values, row r for
  * a_r = a_init + r (a_final - a_init) / (nfilter_a - 1), and a force at scale
- * factor a uses the nearest row (nfilter_a <= 1: one row for all a).  net is three
+ * factor a uses the nearest row (nfilter_a <= 1: one row for all a).  With
+ * params = wpack = NULL the correction is the filter alone: no net, no net
+ * buffers in the workspace and no mesh-size condition (the form for meshes
+ * whose net activations would not fit).  net is three
  * circular 3x3x3 convolutions 4 -> 16 -> 16 -> 3 with ReLU, BF16 weights and
  * activations, FP32 accumulation.  params (device, FP32, COLA_NET_NPARAMS):
  *   W1 [16][4][27] @0, b1 [16] @1728, W2 [16][16][27] @1744, b2 [16] @8656,
@@ -98,7 +101,7 @@ typedef struct cola_config {
     double sampling_p;  /* exponent for COLA_SAMPLING_POW */
     uint32_t flags;     /* COLA_FLAG_* */
     cola_cosmology cosmo;
-    const cola_net* net; /* host pointer, required with COLA_FLAG_LEARNED (ng a multiple of 16) */
+    const cola_net* net; /* host pointer, required with COLA_FLAG_LEARNED (ng a multiple of 16 with a net) */
 } cola_config;
 
 /* Particle state: four SoA float[3*Np] device arrays.

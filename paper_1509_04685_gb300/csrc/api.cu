@@ -29,12 +29,19 @@ static int check_config(const cola_config* c) {
     if (!(k.omega_m > 0.0) || !(k.h > 0.0) || !(k.sigma8 > 0.0) || !(k.omega_b >= 0.0) || !(k.t_cmb > 0.0))
         return COLA_EINVAL;
     if (c->flags & COLA_FLAG_LEARNED) {
-        if (c->ng % 16) return COLA_EUNSUPPORTED_SIZE;  // conv bricks of 4 x 8 x 16 voxels
-        if (!c->net || !c->net->params || !c->net->wpack) return COLA_EINVAL;
+        if (!c->net) return COLA_EINVAL;
+        const bool has_net = c->net->params && c->net->wpack;
+        if (!has_net && (c->net->params || c->net->wpack || !c->net->filter)) return COLA_EINVAL;
+        if (has_net && c->ng % 16) return COLA_EUNSUPPORTED_SIZE;  // conv bricks of 4 x 8 x 16 voxels
         if (c->net->filter && (c->net->nfilter < 2 || c->net->nfilter > 64)) return COLA_EINVAL;
         if (c->net->filter && (c->net->nfilter_a < 0 || c->net->nfilter_a > kMaxSteps)) return COLA_EINVAL;
     }
     return COLA_OK;
+}
+
+// the learned correction includes the convolution net (not the filter alone)
+static bool net_on(const cola_config* c) {
+    return (c->flags & COLA_FLAG_LEARNED) && c->net && c->net->params && c->net->wpack;
 }
 
 bool layout_for(const cola_config* cfg, Layout* L) {
@@ -46,7 +53,7 @@ bool layout_for(const cola_config* cfg, Layout* L) {
     L->pk_part = align_up(L->F + 2 * Mg, 4096);
     size_t end = L->F + 3 * Mg;
     L->lrn = 0;
-    if (cfg->flags & COLA_FLAG_LEARNED) {
+    if (net_on(cfg)) {
         L->lrn = align_up(end, 4096);
         end = L->lrn + learned_bytes(ng, nq);
     }
@@ -140,7 +147,7 @@ static int pm_forces_for(const cola_config* cfg, const cola_state* st, double gr
     if (cfg->flags & COLA_FLAG_LEARNED) {
         const double a = 1.5 * cfg->cosmo.omega_m / green;
         return pm_mesh_forces(cfg, st, green, ws, L, s, filter_row(cfg, a), cfg->net->filter ? cfg->net->nfilter : 0,
-                              true);
+                              net_on(cfg));
     }
     return pm_mesh_forces(cfg, st, green, ws, L, s);
 }
@@ -325,8 +332,7 @@ int cola_net_grad(const cola_config* cfg, const cola_state* st, double a, const 
     Layout L;
     int rc = check_ws(cfg, ws, ws_bytes, &L);
     if (rc) return rc;
-    if (!(cfg->flags & COLA_FLAG_LEARNED) || !state_ok(st, false) || !target || !grad || !loss || !(a > 0.0))
-        return COLA_EINVAL;
+    if (!net_on(cfg) || !state_ok(st, false) || !target || !grad || !loss || !(a > 0.0)) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / a;
     if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;

@@ -49,10 +49,15 @@ def filter_row(a: float, nrows: int, a_init: float = 0.05, a_final: float = 1.0)
 
 class LearnedCorrection:
     """Parameters, packed weights, filter table and Adam state of one net.
-    The radial filter has nfilter_a rows, one per scale-factor node."""
+    The radial filter has nfilter_a rows, one per scale-factor node.  The
+    coarse mesh has mesh_factor cells per particle spacing (1 for the paper's
+    PM_grid = 1, 1.5 for the largest run's learned form); the filter nodes are
+    fixed in k L / ng, so a correction fitted in a small box applies to a
+    larger one at the same resolution."""
 
-    def __init__(self, nfilter: int = 16, seed: int = 0, device="cuda", nfilter_a: int = 1):
+    def __init__(self, nfilter: int = 16, seed: int = 0, device="cuda", nfilter_a: int = 1, mesh_factor: float = 1.0):
         self.device = torch.device(device)
+        self.mesh_factor = mesh_factor
         self.params = init_params(seed, device)
         self.wpack = torch.zeros(L.NET_NPACK, dtype=torch.bfloat16, device=self.device)
         self.filter = torch.ones((nfilter_a, nfilter), dtype=torch.float32, device=self.device)
@@ -65,18 +70,17 @@ class LearnedCorrection:
     def pack(self):
         L.cola_net_pack(self.net)
 
+    def ng(self, nq: int) -> int:
+        """Coarse mesh cells per side for nq particles per side."""
+        return int(round(self.mesh_factor * nq))
+
     def config(self, nq: int, box: float, a_init: float = 0.05, n_steps: int = 40, use_net: bool = True):
-        """PM_grid = 1 config using this correction (filter always, net if use_net)."""
+        """Coarse-mesh config using this correction: the filter always, the net
+        if use_net (else the filter alone: no net buffers, no convolutions)."""
         if use_net:
-            return L.make_config(nq, nq, box, a_init, 1.0, n_steps, flags=L.FLAG_LEARNED, net=self.net)
-        zero = LearnedCorrection.__new__(LearnedCorrection)
-        zero.params = torch.zeros_like(self.params)
-        zero.wpack = torch.zeros_like(self.wpack)
-        zero.net = L.make_net(zero.params, zero.wpack, self.filter)
-        L.cola_net_pack(zero.net)
-        cfg = L.make_config(nq, nq, box, a_init, 1.0, n_steps, flags=L.FLAG_LEARNED, net=zero.net)
-        cfg._zero_ref = zero
-        return cfg
+            return L.make_config(nq, self.ng(nq), box, a_init, 1.0, n_steps, flags=L.FLAG_LEARNED, net=self.net)
+        return L.make_config(nq, self.ng(nq), box, a_init, 1.0, n_steps, flags=L.FLAG_LEARNED,
+                             net=L.make_net(None, None, self.filter))
 
     def state_dict(self):
         return {"params": self.params.cpu(), "filter": self.filter.cpu()}
@@ -114,7 +118,7 @@ class FilterFit:
     def __init__(self, corr: LearnedCorrection, nq: int, box: float):
         self.corr, self.nq, self.box = corr, nq, box
         na, nb = corr.filter.shape
-        self.cfg = L.make_config(nq, nq, box, 0.05)
+        self.cfg = L.make_config(nq, corr.ng(nq), box, 0.05)
         self.sim = Simulation(self.cfg, device=corr.device)
         self.sim.init_tables()
         self.basis = torch.empty((nb, 3 * nq**3), dtype=torch.float32, device=corr.device)
@@ -148,12 +152,19 @@ def fit_filter(corr: LearnedCorrection, samples, nq: int, box: float, ridge: flo
     return fit.solve(ridge)
 
 
+def output_node(a_out: float, a_nodes) -> int:
+    """Node whose positions a snapshot at a_out drifts from: the last node
+    a_j <= a_out (the final node for a_out >= a_final)."""
+    return int(np.searchsorted(np.asarray(a_nodes), a_out + 1e-12, side="right") - 1)
+
+
 def fit_filter_runs(corr: LearnedCorrection, seeds, nq: int, box: float, m_fine: int = 3, a_init=0.05, n_steps=40,
-                    ridge: float = 1e-6, keep_nodes=(), device="cuda"):
+                    ridge: float = 1e-6, keep_nodes=(), device="cuda", outputs=(1.0,)):
     """Least-squares filter from plain runs at PM_grid = m_fine, accumulated at
     every node of every run without storing the configurations.  Returns the
-    Samples at keep_nodes (for the net) and each run's final P(k) on an nq^3
-    mesh, {seed: (k, P)}, as by-products."""
+    Samples at keep_nodes (for the net) and each run's P(k) on an nq^3 mesh at
+    the scale factors `outputs` (snapshot drift between nodes), {seed: [(a, k,
+    P), ...]}, as by-products."""
     fit = FilterFit(corr, nq, box)
     cfg = L.make_config(nq, m_fine * nq, box, a_init, 1.0, n_steps)
     sim = Simulation(cfg, device=device)
@@ -161,15 +172,21 @@ def fit_filter_runs(corr: LearnedCorrection, seeds, nq: int, box: float, m_fine:
     for seed in seeds:
         sim.ic(seed)
         tab = sim.table()[:, 0].cpu().numpy()
+        at = {output_node(a, tab): a for a in outputs}
+        final[seed] = []
         for j in range(n_steps):
             a = float(tab[j])
+            if j in at and j < n_steps - 1:
+                k, p, _ = sim.power(nq, a_out=at[j], node=j)
+                final[seed].append((at[j], k.cpu().numpy(), p.cpu().numpy()))
             target = sim.force(a)
             fit.add(sim.d, a, target)
             if j in keep_nodes:
                 kept.append(Sample(sim.d.clone(), a, target.clone()))
             sim.step(j)
-        k, p, _ = sim.power(nq, node=n_steps - 1)
-        final[seed] = (k.cpu().numpy(), p.cpu().numpy())
+        if n_steps - 1 in at:
+            k, p, _ = sim.power(nq, a_out=at[n_steps - 1], node=n_steps - 1)
+            final[seed].append((at[n_steps - 1], k.cpu().numpy(), p.cpu().numpy()))
     fit.solve(ridge)
     del sim
     return kept, final
@@ -182,30 +199,41 @@ def pk_deviation(k, p, p_ref, kmax: float = 1.0):
 
 
 def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: float = 1.0, rounds: int = 2,
-                     device="cuda"):
+                     device="cuda", use_net: bool = True):
     """Fit the least-squares filter's outcome on the training seeds: with
-    T' = (1 + g (T - 1)) (1 + c (k / k_Ny)^2) for k <= k_Ny (the boost held at
-    its k_Ny value beyond), choose g, c by alternating golden-section searches
-    that minimise the mean final-P(k) deviation of the corrected 1x runs from
-    the seeds' own fine runs (`final` from fit_filter_runs).  Returns (g, c)."""
+    T'_r = (1 + g (T_r - 1)) (1 + c (a_r / a_f) (k / k_Ny)^2) for k <= k_Ny (the
+    boost held at its k_Ny value beyond; a_r the scale factor of filter row r),
+    choose g, c by alternating golden-section searches
+    that minimise the mean P(k) deviation, over the seeds and their output
+    times, of the corrected coarse runs from the seeds' own fine runs (`final`
+    from fit_filter_runs, outputs in increasing a).  Returns (g, c)."""
     na, nb = corr.filter.shape
     base = corr.filter.clone()
     kn = torch.arange(nb, dtype=torch.float64, device=corr.device) * (np.sqrt(3.0) / (nb - 1))  # k / k_Ny
-    shape = torch.clamp(kn, max=1.0) ** 2
-    cfg = corr.config(nq, box)
+    ar = 0.05 + torch.arange(na, dtype=torch.float64, device=corr.device) * (0.95 / max(na - 1, 1))  # row a
+    # the sub-cell clustering the boost stands in for grows with time: scale it by a_r / a_final
+    shape = (ar if na > 1 else torch.ones_like(ar))[:, None] * (torch.clamp(kn, max=1.0) ** 2)[None, :]
+    cfg = corr.config(nq, box, use_net=use_net)
     sim = Simulation(cfg, device=device)
 
     def apply(g, c):
-        corr.filter.copy_(((1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)[None, :]).float())
+        corr.filter.copy_(((1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)).float())
 
     def objective(g, c):
         apply(g, c)
         dev = []
-        for seed, (k, p3) in final.items():
+        tab = None
+        for seed, outs in final.items():
             sim.ic(seed)
-            sim.run()
-            _, p, _ = sim.power(nq, node=cfg.n_steps - 1)
-            dev.append(pk_deviation(k, p.cpu().numpy(), p3, kmax))
+            if tab is None:
+                tab = sim.table()[:, 0].cpu().numpy()
+            j = 0
+            for a_out, k, p3 in outs:
+                node = output_node(a_out, tab)
+                sim.run(range(j, node))
+                j = node
+                _, p, _ = sim.power(nq, a_out=a_out, node=node)
+                dev.append(pk_deviation(k, p.cpu().numpy(), p3, kmax))
         return float(np.mean(dev))
 
     def golden(f, lo, hi, iters=8):
@@ -225,8 +253,8 @@ def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: 
 
     g, c = 1.0, 0.0
     for _ in range(rounds):
-        c, _ = golden(lambda x: objective(g, x), -0.2, 2.0)
-        g, _ = golden(lambda x: objective(x, c), 0.5, 3.0)
+        c, _ = golden(lambda x: objective(g, x), -0.3, 4.0)
+        g, _ = golden(lambda x: objective(x, c), 0.0, 3.0)
     apply(g, c)
     torch.cuda.synchronize()
     del sim
@@ -257,10 +285,11 @@ def train(corr: LearnedCorrection, samples, nq: int, box: float, iters: int = 50
 
 
 def force_errors(corr: LearnedCorrection, samples, nq: int, box: float):
-    """Mean relative L2 force error against the fine force for the plain 1x
-    mesh, the 1x mesh with the filter, and the full correction."""
+    """Mean relative L2 force error against the fine force for the plain
+    coarse mesh, the coarse mesh with the filter, and the full correction
+    (keys name the PM_grid = 1 case)."""
     sims = {
-        "plain_1x": Simulation(L.make_config(nq, nq, box, 0.05), device=corr.device),
+        "plain_1x": Simulation(L.make_config(nq, corr.ng(nq), box, 0.05), device=corr.device),
         "filter_1x": Simulation(corr.config(nq, box, use_net=False), device=corr.device),
         "learned_1x": Simulation(corr.config(nq, box), device=corr.device),
     }

@@ -122,6 +122,32 @@ def test_scale_factor_filter_rows_vs_oracle():
         assert rel_l2(got, ref) < 1e-5, a
 
 
+def test_filter_only_correction_on_a_1p5x_mesh_vs_oracle():
+    # the correction without a net (params = wpack = NULL) on a 1.5x mesh whose
+    # size is not a multiple of 16 (the net's bricks would need one)
+    nq, ng, L, a = 20, 30, 60.0, 0.5
+    plin = cm.LinearPower(COSMO)
+    D1, _, D2, _ = cm.Growth(COSMO)(np.array([a]))
+    d = f32(lpt.initial_conditions(8, nq, L, plin, D1[0], D2[0])["d"])
+    rows = np.stack([1.0 + 0.25 * np.cos(np.arange(8) + r) for r in range(2)])
+    filt = torch.tensor(rows, dtype=torch.float32, device="cuda")
+    net = C.make_net(None, None, filt)
+    sim = C.Simulation(C.make_config(nq, ng, L, 0.05, flags=C.FLAG_LEARNED, net=net))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    green = 1.5 * COSMO.omega_m / a
+    u = pm.mesh_coords(d, nq, ng, L)
+    delta = pm.cic_deposit(u, ng) * (ng / nq) ** 3 - 1.0
+    F = pm.force_mesh_from_delta(delta, L, green, filt=rows[ol.filter_row(a, 2, 0.05, 1.0)])
+    ref = np.stack([pm.cic_gather(F[j], u) for j in range(3)])
+    assert rel_l2(host(sim.force(a)), ref) < 1e-5
+    # no net: its gradient call is refused
+    grad = torch.zeros(C.NET_NPARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(C.ColaError):
+        C.cola_net_grad(sim.cfg, sim.state, a, dev(ref), grad, loss, sim.ws)
+
+
 def test_net_gradients_vs_oracle():
     nq, L, a = 32, 64.0, 0.5
     d, T = _setup(nq, L, a, seed=4)
