@@ -46,6 +46,45 @@ WORKLOADS = {
 }
 
 
+def max_over_ranks(x: float, dist, device="cuda") -> float:
+    """The slowest rank's value (every rank receives it); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device="cuda") -> float:
+    """The sum over ranks (every rank receives it); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def replica_value(units_local: float, ms_local: float, dist, device="cuda") -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units of all ranks
+    over the slowest rank's time.  Returns (value per second, max ms)."""
+    ms = max_over_ranks(ms_local, dist, device)
+    return sum_over_ranks(units_local, dist, device) / (ms * 1e-3), ms
+
+
+def replica_seed(rank: int) -> int:
+    """Realisation of a rank: seed 1 + rank (rank 0 runs the single-GPU seed)."""
+    return 1 + rank
+
+
+def members_of(rank: int, world: int):
+    """The ensemble members a rank advances: member i on rank i mod world."""
+    return [m for i, m in enumerate(ensemble_members()) if i % world == rank]
+
+
 def ensemble_members():
     out = []
     for i in range(48):
@@ -58,7 +97,7 @@ def ensemble_members():
 def run_ensemble(args, rank, world, C, torch, dist):
     """One timed step = one graph launch replaying the 2LPT set-up and all 40
     nodes of this rank's members (members i = rank mod world)."""
-    mem = [m for i, m in enumerate(ensemble_members()) if i % world == rank]
+    mem = members_of(rank, world)
     cfgs = [C.make_config(nq, ng, box, A_INIT, 1.0, N_NODES) for nq, ng, box, _ in mem]
     sims = [C.Simulation(c) for c in cfgs]
     # autotune the tile width of every mesh size once
@@ -95,15 +134,7 @@ def run_ensemble(args, rank, world, C, torch, dist):
     for sm in sims:
         if sm.status() != 0:
             raise SystemExit("device status after ensemble")
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    ps_local = sum(nq**3 for nq, _, _, _ in mem) * N_NODES
-    ps = torch.tensor([float(ps_local)], device="cuda")
-    if dist:
-        dist.all_reduce(ps)
-    value = float(ps.item()) * nrep / (ms * 1e-3)
+    value, ms = replica_value(float(sum(nq**3 for nq, _, _, _ in mem) * N_NODES * nrep), ms, dist)
     if rank == 0:
         print(json.dumps({
             "metric": "particle-steps/s (48-seed uneven ensemble, one CUDA-graph launch per run)", "value": value,
@@ -500,7 +531,7 @@ def main():
     w = WORKLOADS[args.workload]
     cfg = C.make_config(w["nq"], w["ng"], w["box"], A_INIT, 1.0, N_NODES)
     sim = C.Simulation(cfg, device=f"cuda:{local}")
-    sim.ic(seed=1 + rank)
+    sim.ic(seed=replica_seed(rank))
     for j in range(args.warmup):
         sim.step(j % N_NODES)
     torch.cuda.synchronize()
@@ -528,10 +559,8 @@ def main():
     status = sim.status()
     if status != 0:
         raise SystemExit(f"device status {status}: {C.cola_strerror(status)}")
+    value, ms = replica_value(float(w["nq"] ** 3 * args.steps), ms, dist)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
 
     per_kernel = {}
@@ -545,7 +574,6 @@ def main():
     peak, peak_kind = peaks()
     achieved = alg / (dom_avg_ms * 1e-3) / 1e9
     np_total = w["nq"] ** 3 * world
-    value = np_total * args.steps / (ms * 1e-3)
     step_ms = ms / args.steps
     bref = step_reference_bytes(w["nq"], w["ng"])
 
@@ -569,11 +597,7 @@ def main():
             o.copy_(x, non_blocking=True)
     e3.record()
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist)
     h2d = sum(x.numel() * x.element_size() for x in hst)
     d2h = sum(x.numel() * x.element_size() for x in out)
 
