@@ -61,3 +61,63 @@ def test_jing_correction_flattens_poisson_shot_noise():
     sel = nm > 100
     assert np.all(np.abs(pj[sel] / shot - 1) < 6 / np.sqrt(nm[sel]) + 0.01)
     assert praw[sel][-1] / shot < 0.8  # the raw estimator is suppressed near Nyquist
+
+
+@pytest.mark.parametrize("axis,l2,l4", [(2, 1.0, 1.0), (0, -0.5, 3.0 / 8.0)])
+def test_plane_wave_multipoles_are_legendre_values(axis, l2, l4):
+    # a wave along z has mu = +-1, one along x has mu = 0: P2/P0 = 5 L2(mu), P4/P0 = 9 L4(mu)
+    ng, L, eps = 16, 64.0, 0.02
+    x = np.arange(ng)
+    shape = [1, 1, 1]
+    shape[axis] = ng
+    delta = eps * np.cos(2 * np.pi * 3 * x / ng).reshape(shape) * np.ones((ng, ng, ng))
+    k, p0, p2, p4, nm = power.multipoles_from_delta(delta, L)
+    _, p, _ = power.power_from_delta(delta, L)
+    np.testing.assert_allclose(p0, p, rtol=1e-12, atol=1e-30)
+    assert p0[2] > 0
+    assert p2[2] / p0[2] == pytest.approx(5 * l2, rel=1e-12)
+    assert p4[2] / p0[2] == pytest.approx(9 * l4, rel=1e-12)
+
+
+def test_isotropic_white_noise_has_no_quadrupole():
+    ng, L = 32, 100.0
+    delta = np.random.default_rng(4).standard_normal((ng, ng, ng))
+    k, p0, p2, p4, nm = power.multipoles_from_delta(delta, L)
+    sel = nm > 500
+    # mode-by-mode scatter of |delta|^2 L_l(mu): 5 / sqrt(n) (quadrupole), 9 / sqrt(n) (hexadecapole)
+    assert np.all(np.abs(p2[sel] / p0[sel]) < 5 * 5 / np.sqrt(nm[sel]))
+    assert np.all(np.abs(p4[sel] / p0[sel]) < 5 * 9 / np.sqrt(nm[sel]))
+
+
+def test_small_amplitude_zeldovich_field_obeys_kaiser():
+    # x = q + D Psi, velocity f D Psi: delta_s(k) = (1 + f mu^2) delta(k) to first order in the amplitude,
+    # so every bin's multipoles equal the real-space mode sums weighted by (1 + f mu^2)^2 L_l(mu)
+    from oracle import cosmology as cm
+    from oracle import lpt
+    c = cm.Cosmology()
+    g = cm.Growth(c)
+    a, nq, ng, L = 0.5, 32, 64, 256.0
+    D1, D1p, D2, D2p = (x[0] for x in g(np.array([a])))
+    st = lpt.initial_conditions(3, nq, L, cm.LinearPower(c), D1, D2)
+    scale = 1e-3  # linear regime: displacements far below a cell
+    psi1 = st["psi1"] * scale
+    state = {"d": D1 * psi1, "v": np.zeros_like(psi1), "psi1": psi1, "psi2": np.zeros_like(psi1)}
+    ds = power.redshift_space_displacement(state, a, D1p, D2p, c)
+    f = a * D1p / D1
+    # the redshift-space shift is f times the real-space displacement along z
+    np.testing.assert_allclose(ds[2] - state["d"][2], f * state["d"][2], rtol=1e-10)
+    k, p0, p2, p4, nm = power.power_multipoles(ds, nq, ng, L)
+    from oracle.pm import density_contrast
+    delta_r = density_contrast(state["d"], nq, ng, L)
+    # Kaiser weights applied mode by mode to the real-space field
+    dk = np.fft.rfftn(delta_r)
+    nf = np.fft.fftfreq(ng, d=1.0 / ng)
+    nz = np.arange(ng // 2 + 1)
+    n2 = nf[:, None, None] ** 2 + nf[None, :, None] ** 2 + nz[None, None, :] ** 2
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = np.where(n2 > 0, nz[None, None, :] / np.sqrt(n2), 0.0)
+    kaiser = np.fft.irfftn(dk * (1 + f * mu**2), s=delta_r.shape, axes=(0, 1, 2))
+    _, e0, e2, e4, _ = power.multipoles_from_delta(kaiser, L)
+    sel = (k < 0.25 * np.pi * ng / L) & (nm > 50)
+    np.testing.assert_allclose(p0[sel], e0[sel], rtol=5e-3)
+    np.testing.assert_allclose(p2[sel], e2[sel], rtol=2e-2)
