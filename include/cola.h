@@ -155,6 +155,18 @@ int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t no
                         int32_t ng_pk, int32_t flags, double* k, double* pk, double* nmodes,
                         int32_t nbins, void* ws, size_t ws_bytes, void* stream);
 
+/* Redshift-space multipoles about the z axis (the paper's RSD study, Eq. 5;
+ * a plane-parallel line of sight along z): as cola_power_spectrum, but each
+ * particle is first moved along z by its peculiar velocity,
+ *   s_z = x_z + p_z / (a^2 E(a)),  p = v + a^3 E(a) (D1'(a) Psi1 + D2'(a) Psi2)
+ * (p = v with COLA_FLAG_PM_ONLY), at a = a_out, and the shells accumulate
+ *   P_l(k) = (2l + 1) <P L_l(mu)>, mu = k_z / |k|, l = 0, 2, 4
+ * into p0, p2, p4 (DEVICE float64[nbins]).  Needs the full state (v, psi1,
+ * psi2).  Same bins, flags, workspace and errors as cola_power_spectrum. */
+int cola_power_multipoles(const cola_config* cfg, const cola_state* st, int32_t node, double a_out,
+                          int32_t ng_pk, int32_t flags, double* k, double* p0, double* p2, double* p4,
+                          double* nmodes, int32_t nbins, void* ws, size_t ws_bytes, void* stream);
+
 /* Density contrast delta = rho (ng/nq)^3 - 1 of the state on the force mesh,
  * written unpadded as float[ng^3] (C order).  The deposit is deterministic
  * (fixed-point, 2^40 per particle). */

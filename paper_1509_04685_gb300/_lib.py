@@ -89,6 +89,7 @@ def _load():
         "cola_ensemble_destroy": ([vp], None),
         "cola_fft_autotune": ([i32, vp, vp, sz, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "cola_fft_set_tile": ([i32, i32], ctypes.c_int),
+        "cola_power_multipoles": ([cfgp, stp, i32, dbl, i32, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp], ctypes.c_int),
         "cola_profile_start": ([i32], ctypes.c_int),
         "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
         "cola_num_kernel_ids": ([], i32),
@@ -249,6 +250,13 @@ def cola_power_spectrum(cfg, st: cola_state, node: int, a_out: float, ng_pk: int
     _check(LIB.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), node, a_out, ng_pk, flags, _ptr(k), _ptr(pk),
                                    _ptr(nmodes), ng_pk // 2, _ptr(ws), ws.numel() * ws.element_size(),
                                    _stream(stream)), "cola_power_spectrum")
+
+
+def cola_power_multipoles(cfg, st: cola_state, node: int, a_out: float, ng_pk: int, flags: int, k, p0, p2, p4,
+                          nmodes, ws, stream=None):
+    _check(LIB.cola_power_multipoles(ctypes.byref(cfg), ctypes.byref(st), node, a_out, ng_pk, flags, _ptr(k),
+                                     _ptr(p0), _ptr(p2), _ptr(p4), _ptr(nmodes), k.numel(), _ptr(ws),
+                                     ws.numel() * ws.element_size(), _stream(stream)), "cola_power_multipoles")
 
 
 def cola_density(cfg, st: cola_state, delta, ws, stream=None):

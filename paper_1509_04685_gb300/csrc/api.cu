@@ -229,19 +229,23 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
                                     status_ptr(ws), s);
 }
 
-int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t node, double a_out, int32_t ng_pk,
+}  // extern "C"
+
+// P(k) (or, with p2/p4, the redshift-space multipoles) of the state at node,
+// drifted to a_out if a_out differs from the node's scale factor
+static int power_common(const cola_config* cfg, const cola_state* st, int32_t node, double a_out, int32_t ng_pk,
                         int32_t flags, double* k, double* pk, double* nmodes, int32_t nbins, void* ws,
-                        size_t ws_bytes, void* stream) {
+                        size_t ws_bytes, cudaStream_t s, double* p2, double* p4) {
     Layout L;
     int rc = check_ws(cfg, ws, ws_bytes, &L);
     if (rc) return rc;
-    if (!state_ok(st, false) || !k || !pk || !nmodes) return COLA_EINVAL;
+    const bool rsd = p2 && p4;
+    if (!state_ok(st, rsd) || !k || !pk || !nmodes) return COLA_EINVAL;
     if (!mesh_ok(ng_pk) || ng_pk > cfg->ng) return COLA_EUNSUPPORTED_SIZE;
     if (nbins != ng_pk / 2 || node < 0 || node >= cfg->n_steps || (flags & ~3)) return COLA_EINVAL;
-    cudaStream_t s = S(stream);
     const double a_node = host_node_a(cfg, node);
     const double* snap = nullptr;
-    if (std::fabs(a_out - a_node) > 1e-12 * a_node) {
+    if (rsd || std::fabs(a_out - a_node) > 1e-12 * a_node) {
         if (!(a_out > 0.0) || !state_ok(st, true)) return COLA_EINVAL;
         double* sp = reinterpret_cast<double*>(wsp(ws, kHdrSnap));
         if ((rc = launch_snapshot_coeffs(cfg, a_node, a_out, sp, s))) return rc;
@@ -253,7 +257,7 @@ int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t no
     if (rc) return rc;
     const double ratio = (double)ng_pk / (double)cfg->nq;
     if ((rc = launch_deposit_ex(st->d, st->v, st->psi1, st->psi2, dep, cfg->nq, ng_pk, cfg->box, snap,
-                                status_ptr(ws), s)))
+                                status_ptr(ws), s, rsd)))
         return rc;
     const long long Ppk = fft_pitch(ng_pk);
     if ((rc = fft_z_r2c(dep, mk, ng_pk, (float)(ratio * ratio * ratio / 1099511627776.0), tw, s, Ppk,
@@ -262,7 +266,23 @@ int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t no
     if ((rc = fft_strided(mk, ng_pk, 1, -1, tw, s))) return rc;
     if ((rc = fft_strided(mk, ng_pk, 0, -1, tw, s))) return rc;
     return launch_power(mk, ng_pk, Ppk, cfg->box, flags, reinterpret_cast<double*>(wsp(ws, L.pk_part)), k, pk, nmodes,
-                        nbins, s);
+                        nbins, s, p2, p4);
+}
+
+extern "C" {
+
+int cola_power_spectrum(const cola_config* cfg, const cola_state* st, int32_t node, double a_out, int32_t ng_pk,
+                        int32_t flags, double* k, double* pk, double* nmodes, int32_t nbins, void* ws,
+                        size_t ws_bytes, void* stream) {
+    return power_common(cfg, st, node, a_out, ng_pk, flags, k, pk, nmodes, nbins, ws, ws_bytes, S(stream), nullptr,
+                        nullptr);
+}
+
+int cola_power_multipoles(const cola_config* cfg, const cola_state* st, int32_t node, double a_out, int32_t ng_pk,
+                          int32_t flags, double* k, double* p0, double* p2, double* p4, double* nmodes, int32_t nbins,
+                          void* ws, size_t ws_bytes, void* stream) {
+    if (!p2 || !p4) return COLA_EINVAL;
+    return power_common(cfg, st, node, a_out, ng_pk, flags, k, p0, nmodes, nbins, ws, ws_bytes, S(stream), p2, p4);
 }
 
 int cola_density(const cola_config* cfg, const cola_state* st, float* delta, void* ws, size_t ws_bytes,

@@ -447,7 +447,7 @@ constexpr int kMaxSteps = 2048;
 constexpr int kTableCols = 12;
 constexpr size_t kHdrStatus = 0;          // int: latched device status
 constexpr size_t kHdrSigmaAmp = 64;       // double: P(k) amplitude A (sigma8 normalisation)
-constexpr size_t kHdrSnap = 128;          // 3 doubles: snapshot drift coefficients (dr, dD1, dD2)
+constexpr size_t kHdrSnap = 128;          // 6 doubles: snapshot drift (dr, dD1, dD2), redshift-space (cv, c1, c2)
 constexpr size_t kHdrGrowthScratch = 256; // small FP64 scratch for the snapshot growth call
 constexpr size_t kHdrFilter = 1024;       // radial filter basis table (<= 64 floats)
 constexpr size_t kHdrTable = 4096;        // kMaxSteps x kTableCols doubles
@@ -558,8 +558,9 @@ int fft_x_green(float2* F, int n, float gscale, float kf, const float2* tw, cuda
 int fft_y_inverse_force(float2* F, int n, const float2* tw, cudaStream_t s, bool psi, float kf);
 __host__ __device__ __forceinline__ FRow force_rows(int ng) { return FRow{ng, xblock_shift(ng), 3}; }
 
+// snap (optional): drift to an output time; rsd: also shift along z into redshift space (snap[3..5])
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
-                      int nq, int ng, double box, const double* snap, int* status, cudaStream_t s);
+                      int nq, int ng, double box, const double* snap, int* status, cudaStream_t s, bool rsd = false);
 // F: interleaved force mesh, real view, component c of (ix, iy) at ((ix n + iy) 3 + c) 2P floats
 int launch_gather(const float2* F, const float* d, float* out, int nq, int ng, double box, cudaStream_t s);
 int launch_gather_kick_drift(const float2* F, cola_state st, const double* row, int nq, int ng, double box, int last,
@@ -572,8 +573,9 @@ int launch_adjoint_deposit(const float* d, const float* res, unsigned long long*
 int launch_tables(const cola_config* cfg, double* table, cudaStream_t s);
 int launch_snapshot_coeffs(const cola_config* cfg, double a_node, double a_out, double* snap, cudaStream_t s);
 int launch_ic(const cola_config* cfg, uint64_t seed, cola_state st, void* ws, const Layout& L, cudaStream_t s);
+// p2, p4 (optional, both or neither): quadrupole and hexadecapole about the z axis
 int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
-                 double* nmodes, int nbins, cudaStream_t s);
+                 double* nmodes, int nbins, cudaStream_t s, double* p2 = nullptr, double* p4 = nullptr);
 size_t power_partial_bytes(int nbins);
 
 // learned coarse-mesh correction (learned.cu)

@@ -173,7 +173,8 @@ int launch_tables(const cola_config* cfg, double* table, cudaStream_t s) {
     return check_launch();
 }
 
-// Snapshot drift from a_node to a_out: (Dr(a_node, a_out), D1(a_out)-D1(a_node), D2(a_out)-D2(a_node)).
+// Snapshot drift from a_node to a_out: (Dr(a_node, a_out), D1(a_out)-D1(a_node), D2(a_out)-D2(a_node)),
+// then the redshift-space coefficients at a_out (1 / (a^2 E), a D1'(a), a D2'(a)).
 __global__ void k_snapshot(double* snap, double a_node, double a_out, CosmoD c, int pm_only) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double lo = fmin(a_node, a_out), hi = fmax(a_node, a_out);
@@ -198,6 +199,16 @@ __global__ void k_snapshot(double* snap, double a_node, double a_out, CosmoD c, 
     snap[0] = sign * dr;
     snap[1] = pm_only ? 0.0 : sign * (D1hi - D1lo) / nrm;
     snap[2] = pm_only ? 0.0 : sign * (D2hi - D2lo) / (nrm * nrm);
+    // redshift-space shift along the line of sight at a_out: p_z / (a^2 E) with the full
+    // momentum p = v + a^3 E (D1' Psi1 + D2' Psi2), i.e. v_z / (a^2 E) + a (D1' Psi1_z + D2' Psi2_z)
+    double u[6];
+    growth_init(u);
+    rk4_to(u, log(kAEarly), log(a_out), c, kHEarly);
+    const double dD1 = (u[0] + u[1]) / nrm;                // dD1/da at a_out
+    const double dD2 = a_out * (2.0 * u[2] + u[3]) / (nrm * nrm);  // dD2/da at a_out
+    snap[3] = 1.0 / (a_out * a_out * E_of(a_out, c));
+    snap[4] = pm_only ? 0.0 : a_out * dD1;
+    snap[5] = pm_only ? 0.0 : a_out * dD2;
 }
 
 int launch_snapshot_coeffs(const cola_config* cfg, double a_node, double a_out, double* snap, cudaStream_t s) {

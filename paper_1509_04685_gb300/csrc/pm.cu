@@ -51,7 +51,9 @@ __device__ __forceinline__ bool particle_cic(long long p, int nq, int ng, float 
 // deposit (optionally drifting to an output time on the fly:
 // d_out = d + dr v + dD1 psi1 + dD2 psi2, coefficients in snap[0..2])
 // --------------------------------------------------------------------------
-template <bool SNAP>
+// RSD (with SNAP): then shift along z into redshift space,
+// dz += cv v_z + c1 psi1_z + c2 psi2_z (coefficients in snap[3..5])
+template <bool SNAP, bool RSD = false>
 __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__ v, const float* __restrict__ psi1,
                           const float* __restrict__ psi2, unsigned long long* __restrict__ dep, int nq, int ng,
                           float inv_cell, long long np, const double* __restrict__ snap, int* status) {
@@ -69,6 +71,7 @@ __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__
         dx[a] = d[a * np + p];
         if (SNAP) dx[a] += dr * v[a * np + p] + d1 * psi1[a * np + p] + d2 * psi2[a * np + p];
     }
+    if (RSD) dx[2] += (float)snap[3] * v[2 * np + p] + (float)snap[4] * psi1[2 * np + p] + (float)snap[5] * psi2[2 * np + p];
     Cic c;
     if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
         set_status(status, COLA_ENONFINITE);
@@ -99,13 +102,15 @@ __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__
 }
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
-                      int nq, int ng, double box, const double* snap, int* status, cudaStream_t s) {
+                      int nq, int ng, double box, const double* snap, int* status, cudaStream_t s, bool rsd) {
     const long long np = (long long)nq * nq * nq;
     const int T = 256;
     const unsigned grid = (unsigned)((np + T - 1) / T);
     const float inv_cell = (float)((double)ng / box);
     ProfScope ps(kKDeposit, s);
-    if (snap)
+    if (snap && rsd)
+        k_deposit<true, true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status);
+    else if (snap)
         k_deposit<true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status);
     else
         k_deposit<false><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, nullptr, status);

@@ -7,7 +7,9 @@
 // the kz = 0 and kz = Nyquist planes.  P(k_n) = |delta_k|^2 L^3 / ng^6.
 // A fixed grid of blocks each accumulates its share of the modes into FP32
 // shared-memory bins; the per-block partials are then summed in FP64 in a
-// fixed block order.
+// fixed block order.  With MULTI the bins also take P L_2(mu) and P L_4(mu),
+// mu = n_z / |n| (line of sight z): the redshift-space multipoles
+// P_l = (2l + 1) <P L_l(mu)> of the paper's RSD study (Eq. 5).
 #include "cola_common.cuh"
 
 namespace cola {
@@ -15,10 +17,12 @@ namespace cola {
 constexpr int kPkBlocks = 608;  // 4 blocks per SM on a 152-SM GB300
 constexpr int kPkThreads = 256;
 
+template <bool MULTI>
 __global__ void k_pk_shells(const float2* __restrict__ mk, int ng, long long P, float amp_scale, float kf, int flags,
                             int nbins, double* __restrict__ part) {
-    extern __shared__ float bins[];  // 3 x nbins: sum w, sum w k, sum w P
-    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) bins[i] = 0.f;
+    constexpr int NA = MULTI ? 5 : 3;  // sum w, sum w k, sum w P [, sum w P L2, sum w P L4]
+    extern __shared__ float bins[];
+    for (int i = threadIdx.x; i < NA * nbins; i += blockDim.x) bins[i] = 0.f;
     __syncthreads();
     const int H = ng / 2 + 1;
     const long long total = (long long)ng * ng * H;
@@ -68,48 +72,67 @@ __global__ void k_pk_shells(const float2* __restrict__ mk, int ng, long long P, 
         atomicAdd(&bins[i - 1], w);
         atomicAdd(&bins[nbins + i - 1], w * kmag);
         atomicAdd(&bins[2 * nbins + i - 1], w * p);
+        if (MULTI) {
+            const float mu2 = (float)((double)kz * kz / (double)n2);
+            const float l2 = 1.5f * mu2 - 0.5f;
+            const float l4 = (35.f * mu2 * mu2 - 30.f * mu2 + 3.f) * 0.125f;
+            atomicAdd(&bins[3 * nbins + i - 1], w * p * l2);
+            atomicAdd(&bins[4 * nbins + i - 1], w * p * l4);
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x)
-        part[(size_t)blockIdx.x * 3 * nbins + i] = (double)bins[i];
+    for (int i = threadIdx.x; i < NA * nbins; i += blockDim.x)
+        part[(size_t)blockIdx.x * NA * nbins + i] = (double)bins[i];
 }
 
 __global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nbins, double* k, double* pk,
-                            double* nmodes) {
+                            double* nmodes, double* p2, double* p4) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nbins) return;
-    double w = 0.0, wk = 0.0, wp = 0.0;
+    const int NA = p2 ? 5 : 3;
+    double w = 0.0, wk = 0.0, wp = 0.0, w2 = 0.0, w4 = 0.0;
     for (int b = 0; b < nblocks; ++b) {
-        const double* q = part + (size_t)b * 3 * nbins;
+        const double* q = part + (size_t)b * NA * nbins;
         w += q[i];
         wk += q[nbins + i];
         wp += q[2 * nbins + i];
+        if (p2) {
+            w2 += q[3 * nbins + i];
+            w4 += q[4 * nbins + i];
+        }
     }
     nmodes[i] = w;
     k[i] = w > 0.0 ? wk / w : 0.0;
     pk[i] = w > 0.0 ? wp / w : 0.0;
+    if (p2) {
+        p2[i] = w > 0.0 ? 5.0 * w2 / w : 0.0;
+        p4[i] = w > 0.0 ? 9.0 * w4 / w : 0.0;
+    }
 }
 
 int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
-                 double* nmodes, int nbins, cudaStream_t s) {
+                 double* nmodes, int nbins, cudaStream_t s, double* p2, double* p4) {
     const double ng3 = (double)ng * ng * ng;
     const float amp_scale = (float)(box * sqrt(box) / ng3);  // sqrt(L^3 / ng^6)
     const float kf = (float)(2.0 * 3.14159265358979323846 / box);
-    const size_t smem = (size_t)3 * nbins * sizeof(float);
+    const bool multi = p2 && p4;
+    const size_t smem = (size_t)(multi ? 5 : 3) * nbins * sizeof(float);
+    auto kern = multi ? k_pk_shells<true> : k_pk_shells<false>;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_pk_shells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return COLA_ECUDA;
     {
         ProfScope ps(kKPkShells, s);
-        k_pk_shells<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, flags, nbins, part);
+        kern<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, flags, nbins, part);
     }
     int rc = check_launch();
     if (rc) return rc;
     ProfScope ps(kKPkReduce, s);
-    k_pk_reduce<<<(nbins + 127) / 128, 128, 0, s>>>(part, kPkBlocks, nbins, k, pk, nmodes);
+    k_pk_reduce<<<(nbins + 127) / 128, 128, 0, s>>>(part, kPkBlocks, nbins, k, pk, nmodes, multi ? p2 : nullptr,
+                                                      multi ? p4 : nullptr);
     return check_launch();
 }
 
-size_t power_partial_bytes(int nbins) { return (size_t)kPkBlocks * 3 * nbins * sizeof(double); }
+size_t power_partial_bytes(int nbins) { return (size_t)kPkBlocks * 5 * nbins * sizeof(double); }
 
 }  // namespace cola

@@ -59,6 +59,15 @@ class Simulation:
         L.cola_power_spectrum(self.cfg, self.state, node, a, ng_pk, flags, k, p, n, self.ws, self.stream)
         return k, p, n
 
+    def multipoles(self, ng_pk: int, a_out: float | None = None, flags: int = 0, node: int | None = None):
+        """Redshift-space P0, P2, P4 about the z axis: (k, p0, p2, p4, nmodes)."""
+        nb = ng_pk // 2
+        k, p0, p2, p4, n = (torch.zeros(nb, dtype=torch.float64, device=self.device) for _ in range(5))
+        node = self.node if node is None else node
+        a = self.table()[node, 0].item() if a_out is None else a_out
+        L.cola_power_multipoles(self.cfg, self.state, node, a, ng_pk, flags, k, p0, p2, p4, n, self.ws, self.stream)
+        return k, p0, p2, p4, n
+
     def table(self):
         out = torch.empty((self.cfg.n_steps, 12), dtype=torch.float64, device=self.device)
         L.cola_step_table(self.cfg, out, self.ws, self.stream)

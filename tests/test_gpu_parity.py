@@ -250,6 +250,36 @@ def test_power_spectrum_snapshot_drift(plin, growth):
     np.testing.assert_allclose(p, pr, rtol=5e-5)
 
 
+@pytest.mark.parametrize("pm_only,da", [(False, 0.0), (False, 0.01), (True, 0.0)])
+def test_redshift_space_multipoles_vs_oracle(pm_only, da, plin, growth):
+    # a 2LPT field at a = 0.4 with a random residual momentum: positions moved
+    # along z by p_z / (a^2 E), multipoles about z (at the node or after a snapshot drift)
+    nq, ng, L = 16, 48, 64.0
+    st = _oracle_state(14, nq, L, plin, growth, a=0.4)
+    st["v"] = np.random.default_rng(2).standard_normal(st["d"].shape) * 0.3
+    for key in st:
+        st[key] = f32(st[key])
+    sim = C.Simulation(config(nq, ng, L, flags=C.FLAG_PM_ONLY if pm_only else 0))
+    sim.init_tables()
+    sim.load_state(*(dev(st[k]) for k in ("d", "v", "psi1", "psi2")))
+    node = 15
+    a_node = cm.time_nodes(0.05, 1.0, 40)[node]
+    a_out = a_node + da
+    k, p0, p2, p4, n = (host(x) for x in sim.multipoles(48, a_out=a_out, node=node))
+    ref = dict(st)
+    if da:
+        ref["d"] = ocola.snapshot_displacement(st, a_node, a_out, growth, COSMO, cm.drift_integral)
+    _, D1p, _, D2p = (x[0] for x in growth(np.array([a_out])))
+    ds = power.redshift_space_displacement(ref, a_out, D1p, D2p, COSMO, pm_only=pm_only)
+    kr, r0, r2, r4, nr = power.power_multipoles(ds, nq, 48, L)
+    np.testing.assert_array_equal(n, nr)
+    np.testing.assert_allclose(k, kr, rtol=1e-6)
+    np.testing.assert_allclose(p0, r0, rtol=5e-5)
+    np.testing.assert_allclose(p2, r2, rtol=0, atol=1e-4 * np.abs(r0).max())
+    np.testing.assert_allclose(p4, r4, rtol=0, atol=1e-4 * np.abs(r0).max())
+    assert np.abs(r2).max() > 0.05 * np.abs(r0).max()  # the shift makes a real quadrupole
+
+
 # ---------------------------------------------------------------- run ------
 def test_full_run_small_config_vs_oracle(plin, growth):
     """32^3 particles on a 96^3 mesh, L = 128 Mpc/h, 40 linear steps z = 19 -> 0."""
