@@ -577,6 +577,20 @@ def main():
     step_ms = ms / args.steps
     bref = step_reference_bytes(w["nq"], w["ng"])
 
+    # the outputs' cost: P(k) and the redshift-space multipoles of the current state on
+    # a 1024^3 estimator mesh (the paper's P(k) mesh), timed apart from the step
+    pk_ms = {}
+    ng_pk = min(1024, w["ng"])
+    for name, call in (("power_spectrum", lambda: sim.power(ng_pk)), ("multipoles", lambda: sim.multipoles(ng_pk))):
+        call()
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record()
+        call()
+        e5.record()
+        torch.cuda.synchronize()
+        pk_ms[name] = e4.elapsed_time(e5)
+
     # end to end through the public API with host buffers: per step, the state
     # (d, v, psi1, psi2) comes from pinned host memory and (d, v) go back
     ke = max(1, args.e2e_steps)
@@ -621,6 +635,7 @@ def main():
             "step_roofline": {"B_ref_bytes": bref, "achieved_GBs": bref / (step_ms * 1e-3) / 1e9,
                               "frac": bref / (step_ms * 1e-3) / 1e9 / peak},
             "kernels": per_kernel,
+            "outputs_ms": {"ng_pk": ng_pk, **pk_ms},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
