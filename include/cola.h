@@ -264,6 +264,20 @@ int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* s
  * or a B whose tile buffers exceed the shared memory of one block. */
 int cola_fft_set_tile(int32_t n, int32_t B);
 
+/* Set the traversal order of the particle kernels (deposit, gather, fused
+ * gather + kick + drift, adjoint deposit) for later launches in this process:
+ * each 256-thread block takes a brick of I x J x brick_k Lagrangian sites
+ * (i, j, k; J = min(8, 256 / brick_k), I = 256 / (J brick_k)), bricks are
+ * grouped in cubic tiles of edge^3 sites, tiles in raster order.  For a lattice
+ * of nq^3 sites the tile edge used is the largest power of two not above
+ * `edge` whose padded lattice is within 5% of nq^3 (else the one that pads
+ * least).  The order only shapes the mesh traffic (locality in L2 once
+ * particles have left their lattice sites): every particle is visited once and
+ * the results are bit-identical for any choice.  brick_k is a power of two in
+ * 8..256, edge a power of two in 32..4096 and >= brick_k; 0 restores the
+ * built-in value of either.  Returns COLA_EINVAL for anything else. */
+int cola_particle_set_traversal(int32_t edge, int32_t brick_k);
+
 /* Per-kernel timing (tracing): between cola_profile_start and
  * cola_profile_stop every kernel launch of the library is bracketed by CUDA
  * events on its own stream (at most max_records launches are recorded).

@@ -89,6 +89,7 @@ def _load():
         "cola_ensemble_destroy": ([vp], None),
         "cola_fft_autotune": ([i32, vp, vp, sz, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "cola_fft_set_tile": ([i32, i32], ctypes.c_int),
+        "cola_particle_set_traversal": ([i32, i32], ctypes.c_int),
         "cola_power_multipoles": ([cfgp, stp, i32, dbl, i32, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp], ctypes.c_int),
         "cola_profile_start": ([i32], ctypes.c_int),
         "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
@@ -214,6 +215,10 @@ def cola_fft_autotune(n: int, mesh, ws, stream=None) -> int:
 
 def cola_fft_set_tile(n: int, B: int) -> None:
     _check(LIB.cola_fft_set_tile(n, B), "cola_fft_set_tile")
+
+
+def cola_particle_set_traversal(edge: int, brick_k: int = 0) -> None:
+    _check(LIB.cola_particle_set_traversal(edge, brick_k), "cola_particle_set_traversal")
 
 
 def make_state(d, v=None, psi1=None, psi2=None) -> cola_state:

@@ -145,6 +145,8 @@ int cola_fft_set_tile(int32_t n, int32_t B) {
     return COLA_OK;
 }
 
+int cola_particle_set_traversal(int32_t edge, int32_t brick_k) { return set_particle_traversal(edge, brick_k); }
+
 // Time the y pass of an n^3 mesh for every admissible column width and keep
 // the fastest for this n (used by every later strided pass of that size).
 int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* stream, int32_t* best) {

@@ -25,10 +25,103 @@ struct Cic {
     float f[3];   // fraction towards the upper corner
 };
 
-__device__ __forceinline__ bool particle_cic(long long p, int nq, int ng, float inv_cell, const float dx[3],
+// --------------------------------------------------------------------------
+// Traversal order of the particle kernels.  A block of kTravThreads threads
+// takes a brick of I (i) x J (j) x K (k) lattice sites, K a power of two in
+// 8..256, J = min(8, 256 / K), I = 256 / (J K) (a warp covers consecutive k, so
+// every SoA read is whole 32-byte sectors); bricks are grouped into cubic
+// tiles of E^3 sites (E a power of two), bricks in raster order inside a tile,
+// tiles in raster order over the lattice (k fastest).  The launch grid is
+// (tiles along k x bricks per tile, tiles along j, tiles along i), so blocks
+// are dispatched in that order and each thread finds its site with shifts
+// alone; the padding sites of ragged tiles or bricks exit at once.  Every
+// site is visited exactly once for any K and E: only the order of the memory
+// traffic changes, never a result (the gather is per particle and the deposit
+// adds integers).  Once particles have moved several cells, Lagrangian raster
+// order has the blocks in flight read mesh planes from several i-slabs at
+// once, far more than L2 holds; in tiles the blocks in flight touch a compact
+// region of the mesh and only the tile faces are fetched twice.
+// --------------------------------------------------------------------------
+constexpr int kTravThreads = 256;
+constexpr int kTileEdgeDefault = 256;
+constexpr int kBrickKDefault = 16;
+static int g_tile_edge = kTileEdgeDefault;
+static int g_brick_k = kBrickKDefault;
+
+struct Trav {
+    int nq;
+    int lb;            // log2 of the bricks per tile
+    int lt[3];         // log2 of the tile extent in bricks along i, j, k
+    int lbr[3];        // log2 of the brick extent in sites along i, j, k
+    unsigned grid[3];  // launch grid (x, y, z)
+};
+
+static int ilog2(long long x) {
+    int l = 0;
+    while ((1ll << (l + 1)) <= x) ++l;
+    return l;
+}
+
+// The tile edge actually used for an nq^3 lattice: the largest power of two
+// not above the requested edge (and not below the brick) whose padded lattice
+// is at most 5% larger than nq^3; else the one that pads least.
+static int trav_edge(int nq, int want, int minE) {
+    int best = 0;
+    double best_pad = 1e300;
+    for (int E = want; E >= minE; E >>= 1) {
+        const double n = (double)((nq + E - 1) / E) * E / nq;
+        const double pad = n * n * n;
+        if (pad <= 1.05) return E;
+        if (pad < best_pad) {
+            best_pad = pad;
+            best = E;
+        }
+    }
+    return best;
+}
+
+static Trav make_trav(int nq) {
+    const int K = g_brick_k, J = kTravThreads / K < 8 ? kTravThreads / K : 8, I = kTravThreads / (J * K);
+    const int minE = K > 32 ? K : 32;
+    int want = g_tile_edge > minE ? g_tile_edge : minE;
+    while (want > minE && want / 2 >= nq) want >>= 1;  // no tile larger than the lattice needs
+    const int E = trav_edge(nq, want, minE);
+    Trav t;
+    t.nq = nq;
+    t.lbr[0] = ilog2(I);
+    t.lbr[1] = ilog2(J);
+    t.lbr[2] = ilog2(K);
+    for (int a = 0; a < 3; ++a) t.lt[a] = ilog2(E) - t.lbr[a];
+    t.lb = t.lt[0] + t.lt[1] + t.lt[2];
+    const unsigned ntile = (unsigned)((nq + E - 1) / E);
+    t.grid[0] = ntile << t.lb;
+    t.grid[1] = ntile;
+    t.grid[2] = ntile;
+    return t;
+}
+
+static dim3 trav_grid(const Trav& t) { return dim3(t.grid[0], t.grid[1], t.grid[2]); }
+
+// Lattice site (i, j, k) of this thread; false for padding sites.
+__device__ __forceinline__ bool trav_site(const Trav& t, int idx[3]) {
+    const unsigned x = blockIdx.x;
+    const unsigned tk = x >> t.lb, l = x & ((1u << t.lb) - 1u);
+    const unsigned bk = l & ((1u << t.lt[2]) - 1u);
+    const unsigned bj = (l >> t.lt[2]) & ((1u << t.lt[1]) - 1u);
+    const unsigned bi = l >> (t.lt[2] + t.lt[1]);
+    const unsigned tid = threadIdx.x;
+    idx[0] = (int)((((blockIdx.z << t.lt[0]) + bi) << t.lbr[0]) + (tid >> (t.lbr[2] + t.lbr[1])));
+    idx[1] = (int)((((blockIdx.y << t.lt[1]) + bj) << t.lbr[1]) + ((tid >> t.lbr[2]) & ((1u << t.lbr[1]) - 1u)));
+    idx[2] = (int)((((tk << t.lt[2]) + bk) << t.lbr[2]) + (tid & ((1u << t.lbr[2]) - 1u)));
+    return idx[0] < t.nq && idx[1] < t.nq && idx[2] < t.nq;
+}
+
+__device__ __forceinline__ long long site_index(const int idx[3], int nq) {
+    return ((long long)idx[0] * nq + idx[1]) * nq + idx[2];
+}
+
+__device__ __forceinline__ bool particle_cic(const int idx[3], int nq, int ng, float inv_cell, const float dx[3],
                                              Cic& c) {
-    const long long nq2 = (long long)nq * nq;
-    const int idx[3] = {(int)(p / nq2), (int)((p / nq) % nq), (int)(p % nq)};
     const long long den = 2ll * nq;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -56,9 +149,10 @@ __device__ __forceinline__ bool particle_cic(long long p, int nq, int ng, float 
 template <bool SNAP, bool RSD = false>
 __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__ v, const float* __restrict__ psi1,
                           const float* __restrict__ psi2, unsigned long long* __restrict__ dep, int nq, int ng,
-                          float inv_cell, long long np, const double* __restrict__ snap, int* status) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+                          float inv_cell, long long np, const double* __restrict__ snap, int* status, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
     float dx[3];
     float dr = 0.f, d1 = 0.f, d2 = 0.f;
     if (SNAP) {
@@ -73,7 +167,7 @@ __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__
     }
     if (RSD) dx[2] += (float)snap[3] * v[2 * np + p] + (float)snap[4] * psi1[2 * np + p] + (float)snap[5] * psi2[2 * np + p];
     Cic c;
-    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+    if (!particle_cic(idx, nq, ng, inv_cell, dx, c)) {
         set_status(status, COLA_ENONFINITE);
         return;
     }
@@ -97,23 +191,24 @@ __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__
                 const long long cell = ((long long)ix[a] * ng + iy[b]) * ng + iz[e];
                 atomicAdd(dep + cell, w);
             }
-    const long long cell = ((long long)ix[mx] * ng + iy[my]) * ng + iz[mz];
+    const long long cell = ((long long)(mx ? ix[1] : ix[0]) * ng + (my ? iy[1] : iy[0])) * ng + (mz ? iz[1] : iz[0]);
     atomicAdd(dep + cell, rest);
 }
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
                       int nq, int ng, double box, const double* snap, int* status, cudaStream_t s, bool rsd) {
     const long long np = (long long)nq * nq * nq;
-    const int T = 256;
-    const unsigned grid = (unsigned)((np + T - 1) / T);
+    const Trav tv = make_trav(nq);
+    const dim3 grid = trav_grid(tv);
+    const int T = kTravThreads;
     const float inv_cell = (float)((double)ng / box);
     ProfScope ps(kKDeposit, s);
     if (snap && rsd)
-        k_deposit<true, true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status);
+        k_deposit<true, true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status, tv);
     else if (snap)
-        k_deposit<true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status);
+        k_deposit<true><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, snap, status, tv);
     else
-        k_deposit<false><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, nullptr, status);
+        k_deposit<false><<<grid, T, 0, s>>>(d, v, psi1, psi2, dep, nq, ng, inv_cell, np, nullptr, status, tv);
     return check_launch();
 }
 
@@ -151,12 +246,13 @@ __device__ __forceinline__ void gather3(const float* __restrict__ Fm, int ng, lo
 }
 
 __global__ void k_gather(const float* __restrict__ Fm, const float* __restrict__ d, float* __restrict__ out, int nq,
-                         int ng, long long P2, float inv_cell, long long np) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+                         int ng, long long P2, float inv_cell, long long np, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
     float dx[3] = {d[p], d[np + p], d[2 * np + p]};
     Cic c;
-    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+    if (!particle_cic(idx, nq, ng, inv_cell, dx, c)) {
         out[p] = out[np + p] = out[2 * np + p] = __int_as_float(0x7fc00000);
         return;
     }
@@ -169,10 +265,10 @@ __global__ void k_gather(const float* __restrict__ Fm, const float* __restrict__
 
 int launch_gather(const float2* Fm, const float* d, float* out, int nq, int ng, double box, cudaStream_t s) {
     const long long np = (long long)nq * nq * nq;
-    const int T = 256;
+    const Trav tv = make_trav(nq);
     ProfScope ps(kKGather, s);
-    k_gather<<<(unsigned)((np + T - 1) / T), T, 0, s>>>((const float*)Fm, d, out, nq, ng, 2ll * fft_pitch(ng),
-                                                         (float)((double)ng / box), np);
+    k_gather<<<trav_grid(tv), kTravThreads, 0, s>>>((const float*)Fm, d, out, nq, ng, 2ll * fft_pitch(ng),
+                                                       (float)((double)ng / box), np, tv);
     return check_launch();
 }
 
@@ -185,14 +281,15 @@ int launch_gather(const float2* Fm, const float* d, float* out, int nq, int ng, 
 __global__ void k_gather_kick_drift(const float* __restrict__ Fm, float* __restrict__ d, float* __restrict__ v,
                                     const float* __restrict__ psi1, const float* __restrict__ psi2,
                                     const double* __restrict__ row, int nq, int ng, long long P2, float inv_cell,
-                                    long long np, int last, int pm_only, int* status) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+                                    long long np, int last, int pm_only, int* status, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
     const float c1 = (float)row[2], c2 = (float)row[3], kick = (float)row[4];
     const float drift = (float)row[5], dD1 = (float)row[6], dD2 = (float)row[7];
     float dx[3] = {d[p], d[np + p], d[2 * np + p]};
     Cic c;
-    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) {
+    if (!particle_cic(idx, nq, ng, inv_cell, dx, c)) {
         set_status(status, COLA_ENONFINITE);
         return;
     }
@@ -212,11 +309,11 @@ __global__ void k_gather_kick_drift(const float* __restrict__ Fm, float* __restr
 int launch_gather_kick_drift(const float2* Fm, cola_state st, const double* row, int nq, int ng, double box, int last,
                              int pm_only, int* status, cudaStream_t s) {
     const long long np = (long long)nq * nq * nq;
-    const int T = 256;
+    const Trav tv = make_trav(nq);
     ProfScope ps(kKGatherKD, s);
-    k_gather_kick_drift<<<(unsigned)((np + T - 1) / T), T, 0, s>>>(
+    k_gather_kick_drift<<<trav_grid(tv), kTravThreads, 0, s>>>(
         (const float*)Fm, st.d, st.v, st.psi1, st.psi2, row, nq, ng,
-        2ll * fft_pitch(ng), (float)((double)ng / box), np, last, pm_only, status);
+        2ll * fft_pitch(ng), (float)((double)ng / box), np, last, pm_only, status, tv);
     return check_launch();
 }
 
@@ -243,12 +340,14 @@ int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float sca
 // unit, two's complement in uint64 atomics: order-independent)
 // --------------------------------------------------------------------------
 __global__ void k_adjoint_deposit(const float* __restrict__ d, const float* __restrict__ res,
-                                  unsigned long long* __restrict__ fix3, int nq, int ng, float inv_cell, long long np) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+                                  unsigned long long* __restrict__ fix3, int nq, int ng, float inv_cell, long long np,
+                                  Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
     float dx[3] = {d[p], d[np + p], d[2 * np + p]};
     Cic c;
-    if (!particle_cic(p, nq, ng, inv_cell, dx, c)) return;
+    if (!particle_cic(idx, nq, ng, inv_cell, dx, c)) return;
     const long long n3 = (long long)ng * ng * ng;
     const float wx[2] = {1.f - c.f[0], c.f[0]};
     const float wy[2] = {1.f - c.f[1], c.f[1]};
@@ -276,10 +375,21 @@ __global__ void k_adjoint_deposit(const float* __restrict__ d, const float* __re
 int launch_adjoint_deposit(const float* d, const float* res, unsigned long long* fix3, int nq, int ng, double box,
                            cudaStream_t s) {
     const long long np = (long long)nq * nq * nq;
+    const Trav tv = make_trav(nq);
     ProfScope ps(kKDeposit, s);
-    k_adjoint_deposit<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(d, res, fix3, nq, ng, (float)((double)ng / box),
-                                                                   np);
+    k_adjoint_deposit<<<trav_grid(tv), kTravThreads, 0, s>>>(d, res, fix3, nq, ng, (float)((double)ng / box), np,
+                                                                tv);
     return check_launch();
+}
+
+int set_particle_traversal(int edge, int brick_k) {
+    if (edge == 0) edge = kTileEdgeDefault;
+    if (brick_k == 0) brick_k = kBrickKDefault;
+    if (brick_k < 8 || brick_k > kTravThreads || (brick_k & (brick_k - 1))) return COLA_EINVAL;
+    if (edge < 32 || edge > 4096 || (edge & (edge - 1)) || edge < brick_k) return COLA_EINVAL;
+    g_tile_edge = edge;
+    g_brick_k = brick_k;
+    return COLA_OK;
 }
 
 }  // namespace cola

@@ -57,3 +57,11 @@ def test_entry_points_reject_bad_arguments_without_launching():
                                  fake, size, None) == -1  # nbins != ng_pk/2
     assert C.cola_launch_count() == 0
     assert C.cola_strerror(-6).startswith("non-finite")
+
+
+def test_particle_set_traversal_validates_its_arguments():
+    import paper_1509_04685_gb300 as C
+    for edge, bk in ((-32, 8), (16, 8), (48, 8), (96, 16), (8192, 8), (64, 4), (64, 128), (64, 12), (512, 512)):
+        assert C.LIB.cola_particle_set_traversal(edge, bk) == -1
+    for edge, bk in ((32, 8), (128, 16), (4096, 32), (256, 256), (0, 0)):  # 0 restores the default
+        assert C.LIB.cola_particle_set_traversal(edge, bk) == 0

@@ -126,6 +126,40 @@ def test_density_vs_oracle(nq, ng, L):
     np.testing.assert_array_equal(got, again)  # fixed-point deposit is deterministic
 
 
+# (nq, ng): whole tiles, ragged bricks (nq not a multiple of 8) and ragged tiles
+TRAVERSAL_CASES = [(32, 96), (20, 60), (36, 72), (90, 180)]
+
+
+@pytest.mark.parametrize("nq,ng", TRAVERSAL_CASES)
+def test_particle_traversal_tiles_give_identical_results(nq, ng):
+    # the tile order of the particle kernels visits every particle once, so the
+    # deposit (integer adds), forces and a fused kick + drift are bit-identical
+    L = float(ng)
+    d = f32(random_displacements(5 * nq + 1, nq, 2.0 * L / nq))
+    rng = np.random.default_rng(nq)
+    v, psi1, psi2 = (f32(rng.standard_normal((3, nq**3)) * 0.3) for _ in range(3))
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    out = {}
+    try:
+        for edge, bk in ((0, 0), (32, 8), (32, 16), (64, 8), (64, 32), (128, 64), (256, 256), (4096, 16)):
+            C.cola_particle_set_traversal(edge, bk)
+            sim.load_state(dev(d), dev(v), dev(psi1), dev(psi2))
+            rho = host(sim.density())
+            F = host(sim.force(0.5))
+            sim.step(7)
+            out[edge, bk] = (rho, F, host(sim.d), host(sim.v))
+    finally:
+        C.cola_particle_set_traversal(0, 0)
+    for key, res in out.items():
+        for a, b in zip(res, out[0, 0]):
+            np.testing.assert_array_equal(a, b, err_msg=f"edge, brick {key}")
+    ref = pm.density_contrast(d, nq, ng, L)
+    m3 = (ng / nq) ** 3
+    assert np.abs(out[0, 0][0] - ref).max() < 3e-6 * m3 * (1 + np.abs(ref).max() / m3)
+    assert sim.status() == 0
+
+
 # ---------------------------------------------------------------- force ----
 def _oracle_state(seed, nq, L, plin, growth, a=0.05):
     D1, _, D2, _ = growth(np.array([a]))
