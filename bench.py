@@ -591,29 +591,26 @@ def main():
         torch.cuda.synchronize()
         pk_ms[name] = e4.elapsed_time(e5)
 
-    # end to end through the public API with host buffers: per step, the state
-    # (d, v, psi1, psi2) comes from pinned host memory and (d, v) go back
+    # end to end through the C ABI with host buffers (cola_step_host): per step
+    # the state (d, v, psi1, psi2) goes in from pinned host memory and (d, v)
+    # come back into it before the call returns
     ke = max(1, args.e2e_steps)
     hst = [torch.empty_like(x, device="cpu").pin_memory() for x in (sim.d, sim.v, sim.psi1, sim.psi2)]
     for h, x in zip(hst, (sim.d, sim.v, sim.psi1, sim.psi2)):
         h.copy_(x)
-    out = [torch.empty_like(x, device="cpu").pin_memory() for x in (sim.d, sim.v)]
+    host_state = C.make_state(*hst)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record()
     for i in range(ke):
-        for h, x in zip(hst, (sim.d, sim.v, sim.psi1, sim.psi2)):
-            x.copy_(h, non_blocking=True)
-        sim.step((args.warmup + args.steps + i) % N_NODES)
-        for o, x in zip(out, (sim.d, sim.v)):
-            o.copy_(x, non_blocking=True)
+        sim.step_host(host_state, (args.warmup + args.steps + i) % N_NODES)
     e3.record()
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist)
     h2d = sum(x.numel() * x.element_size() for x in hst)
-    d2h = sum(x.numel() * x.element_size() for x in out)
+    d2h = sum(x.numel() * x.element_size() for x in hst[:2])
 
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()

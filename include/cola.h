@@ -145,6 +145,22 @@ int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float*
 int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes,
               void* stream);
 
+/* End-to-end form of cola_step for a state held in HOST memory: copies
+ * host->d, v, psi1, psi2 (each 3 Nq^3 float32, SoA, HOST pointers; pinned memory
+ * gives asynchronous DMA) into the device state dev (DEVICE pointers, same
+ * layout), runs node `step` exactly as cola_step does, and copies dev->d and
+ * dev->v back into host->d and host->v.  The positions are copied on `stream`,
+ * where the force computation starts at once; v, psi1 and psi2 are copied on
+ * an internal stream meanwhile (it starts after the work already queued on
+ * `stream`), and the kick waits for them.  The copies back are on `stream`;
+ * the call returns after they have completed, so the host arrays hold the new
+ * state on return.  Arguments are validated before any copy
+ * (COLA_EINVAL, COLA_EWORKSPACE, or a config error); if the step itself fails,
+ * dev holds the copied-in state and host is unchanged.  COLA_ECUDA on a failed
+ * copy or synchronisation. */
+int cola_step_host(const cola_config* cfg, const cola_state* host, cola_state* dev, int32_t step, void* ws,
+                   size_t ws_bytes, void* stream);
+
 /* Matter power spectrum (Sec. 2.4) of the state on a CIC mesh of side ng_pk
  * (2 <= ng_pk <= ng, even, 2^a 3^b 5^c).  `node` is the time node the
  * positions sit at; if a_out differs from a_node the positions are first

@@ -69,6 +69,7 @@ def _load():
         "cola_ic_2lpt": ([cfgp, ctypes.c_uint64, stp, vp, sz, vp], ctypes.c_int),
         "cola_pm_force": ([cfgp, stp, dbl, vp, vp, sz, vp], ctypes.c_int),
         "cola_step": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
+        "cola_step_host": ([cfgp, stp, stp, i32, vp, sz, vp], ctypes.c_int),
         "cola_power_spectrum": ([cfgp, stp, i32, dbl, i32, i32, vp, vp, vp, i32, vp, sz, vp], ctypes.c_int),
         "cola_density": ([cfgp, stp, vp, vp, sz, vp], ctypes.c_int),
         "cola_step_table": ([cfgp, vp, vp, sz, vp], ctypes.c_int),
@@ -248,6 +249,13 @@ def cola_pm_force(cfg, st: cola_state, a: float, force, ws, stream=None):
 def cola_step(cfg, st: cola_state, step: int, ws, stream=None):
     _check(LIB.cola_step(ctypes.byref(cfg), ctypes.byref(st), step, _ptr(ws), ws.numel() * ws.element_size(),
                          _stream(stream)), "cola_step")
+
+
+def cola_step_host(cfg, host: cola_state, dev: cola_state, step: int, ws, stream=None):
+    """cola_step on a state in host memory: host holds HOST pointers (copied in,
+    d and v copied back before return), dev the device state."""
+    _check(LIB.cola_step_host(ctypes.byref(cfg), ctypes.byref(host), ctypes.byref(dev), step, _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream(stream)), "cola_step_host")
 
 
 def cola_power_spectrum(cfg, st: cola_state, node: int, a_out: float, ng_pk: int, flags: int, k, pk, nmodes, ws,

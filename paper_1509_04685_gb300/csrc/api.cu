@@ -160,6 +160,25 @@ static const float2* twiddles_for(int n, const cola_config* cfg, void* ws, cudaS
     return tw;
 }
 
+// One node (Eqs. 1-2): the PM forces from the positions, then the fused
+// gather + kick + drift, the only kernel that reads v, psi1 and psi2.  With
+// before_kick, stream s waits for that event first (cola_step_host brings
+// those arrays in meanwhile).
+int step_node(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, cudaStream_t s,
+              cudaEvent_t before_kick) {
+    Layout L;
+    int rc = check_ws(cfg, ws, ws_bytes, &L);
+    if (rc) return rc;
+    if (!state_ok(st, true) || step < 0 || step >= cfg->n_steps) return COLA_EINVAL;
+    const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
+    if (before_kick && cudaStreamWaitEvent(s, before_kick, 0) != cudaSuccess) return COLA_ECUDA;
+    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st,
+                                    table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
+                                    step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
+                                    status_ptr(ws), s);
+}
+
 }  // namespace cola
 
 using namespace cola;
@@ -216,17 +235,7 @@ int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float*
 }
 
 int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, void* stream) {
-    Layout L;
-    int rc = check_ws(cfg, ws, ws_bytes, &L);
-    if (rc) return rc;
-    if (!state_ok(st, true) || step < 0 || step >= cfg->n_steps) return COLA_EINVAL;
-    cudaStream_t s = S(stream);
-    const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
-    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
-    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st,
-                                    table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
-                                    step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
-                                    status_ptr(ws), s);
+    return cola::step_node(cfg, st, step, ws, ws_bytes, S(stream), nullptr);
 }
 
 }  // extern "C"

@@ -570,6 +570,9 @@ int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float sca
 int launch_adjoint_deposit(const float* d, const float* res, unsigned long long* fix3, int nq, int ng, double box,
                            cudaStream_t s);
 int set_particle_traversal(int edge, int brick_k);  // traversal order of the particle kernels (pm.cu)
+// one COLA node; the kick waits for before_kick when given (api.cu)
+int step_node(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, cudaStream_t s,
+              cudaEvent_t before_kick);
 
 int launch_tables(const cola_config* cfg, double* table, cudaStream_t s);
 int launch_snapshot_coeffs(const cola_config* cfg, double a_node, double a_out, double* snap, cudaStream_t s);

@@ -36,6 +36,12 @@ class Simulation:
         L.cola_step(self.cfg, self.state, j, self.ws, self.stream)
         self.node = min(j + 1, self.cfg.n_steps - 1)
 
+    def step_host(self, host: L.cola_state, j: int):
+        """Node j of a state held in host memory (cola_step_host): host's four
+        arrays are copied in, d and v are copied back into them."""
+        L.cola_step_host(self.cfg, host, self.state, j, self.ws, self.stream)
+        self.node = min(j + 1, self.cfg.n_steps - 1)
+
     def run(self, steps=None):
         for j in range(self.cfg.n_steps) if steps is None else steps:
             self.step(j)

@@ -55,6 +55,10 @@ def test_entry_points_reject_bad_arguments_without_launching():
                                  fake, size, None) == -3  # ng_pk > ng
     assert L.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), 0, 0.05, 24, 0, fake, fake, fake, 11,
                                  fake, size, None) == -1  # nbins != ng_pk/2
+    hs = C.cola_state(fake, fake, fake, fake)
+    assert L.cola_step_host(ctypes.byref(cfg), ctypes.byref(hs), ctypes.byref(st), 40, fake, size, None) == -1
+    assert L.cola_step_host(ctypes.byref(cfg), ctypes.byref(hs), ctypes.byref(st), 0, fake, size - 1, None) == -2
+    assert L.cola_step_host(ctypes.byref(cfg), None, ctypes.byref(st), 0, fake, size, None) == -1
     assert C.cola_launch_count() == 0
     assert C.cola_strerror(-6).startswith("non-finite")
 

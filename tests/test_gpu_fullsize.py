@@ -136,18 +136,27 @@ def torch_pm_force(d, nq, ng, L, green, chunk=1 << 23):
     return out
 
 
-@pytest.mark.parametrize("nq,ng,L", [(256, 768, 768.0), (384, 1152, 1152.0), (NQ, NG, L)])
-def test_force_matches_library_fft_reference(nq, ng, L):
+# (nq, ng, L, column widths of the strided and fused passes; 0 = built-in)
+@pytest.mark.parametrize("nq,ng,L,widths", [(256, 768, 768.0, (0,)), (384, 1152, 1152.0, (0,)),
+                                            (NQ, NG, L, (0, 4))])
+def test_force_matches_library_fft_reference(nq, ng, L, widths):
     a = 0.5
     d = dev(random_displacements(5, nq, 0.7 * L / nq))
     s = C.Simulation(C.make_config(nq, ng, L, 0.05))
     s.init_tables()
     s.d.copy_(d)
-    got = s.force(a).double()
-    assert s.status() == 0
+    got = []
+    try:
+        for B in widths:
+            C.cola_fft_set_tile(ng, B)
+            got.append(s.force(a).double().cpu())
+            assert s.status() == 0
+    finally:
+        C.cola_fft_set_tile(ng, 0)
     del s
     torch.cuda.empty_cache()
-    ref = torch_pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / a)
-    rel = (torch.linalg.norm(got - ref) / torch.linalg.norm(ref)).item()
-    assert rel < 1e-5, rel
+    ref = torch_pm_force(d, nq, ng, L, 1.5 * COSMO.omega_m / a).cpu()
+    for B, g in zip(widths, got):
+        rel = (torch.linalg.norm(g - ref) / torch.linalg.norm(ref)).item()
+        assert rel < 1e-5, (B, rel)
 

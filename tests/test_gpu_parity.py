@@ -250,6 +250,27 @@ def test_single_cola_step_vs_oracle(plin, growth):
         assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
 
 
+def test_step_host_matches_device_step(plin, growth):
+    # the host-buffer entry point copies in, runs the same node and copies back
+    nq, ng, L = 32, 96, 128.0
+    ref = _oracle_state(9, nq, L, plin, growth, a=0.3)
+    ref["v"] = np.random.default_rng(1).standard_normal(ref["d"].shape) * 0.05
+    st = {k: f32(ref[k]) for k in ("d", "v", "psi1", "psi2")}
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.load_state(*(dev(st[k]) for k in ("d", "v", "psi1", "psi2")))
+    sim.step(11)
+    want_d, want_v = host(sim.d), host(sim.v)
+    hst = [torch.as_tensor(st[k], dtype=torch.float32).pin_memory() for k in ("d", "v", "psi1", "psi2")]
+    sim.load_state(*(torch.zeros_like(x, device="cuda") for x in hst))  # the call must bring the state in
+    sim.step_host(C.make_state(*hst), 11)
+    np.testing.assert_array_equal(hst[0].numpy(), want_d)
+    np.testing.assert_array_equal(hst[1].numpy(), want_v)
+    np.testing.assert_array_equal(hst[2].numpy(), st["psi1"])  # inputs only
+    np.testing.assert_array_equal(host(sim.d), want_d)
+    assert sim.status() == 0
+
+
 # ---------------------------------------------------------------- P(k) -----
 @pytest.mark.parametrize("flags", [0, C.PK_DECONV_CIC, C.PK_ALIAS_JING])
 def test_power_spectrum_vs_oracle(flags, plin, growth):
