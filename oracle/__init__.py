@@ -19,6 +19,8 @@ the paper and the textbook definitions it relies on:
   gather: the particle-mesh force (Sec. 2.2, Eq. 2 right-hand side).
 * ``cola``      -- the COLA kick-drift-kick loop in the LPT frame (Eqs. 1-2).
 * ``power``     -- the matter P(k) estimator (Sec. 2.4).
+* ``fof``       -- friends-of-friends groups (linking length b of the mean
+  spacing), halo catalogue with Warren masses, mass function (Secs. 2.1, 2.4).
 * ``dft``       -- a direct O(N^2) DFT used to pin numpy's FFT.
 * ``learned``   -- FP64 forward/backward of the learned coarse-mesh force
   correction (k-space filter + 3-layer 3D conv net).  The paper has no such
