@@ -577,11 +577,18 @@ def main():
     step_ms = ms / args.steps
     bref = step_reference_bytes(w["nq"], w["ng"])
 
-    # the outputs' cost: P(k) and the redshift-space multipoles of the current state on
-    # a 1024^3 estimator mesh (the paper's P(k) mesh), timed apart from the step
+    # the outputs' cost, timed apart from the step: P(k) and the redshift-space
+    # multipoles of the current state on a 1024^3 estimator mesh (the paper's P(k)
+    # mesh), and the FoF halos (b = 0.2, >= 100 particles) with their catalogue
     pk_ms = {}
     ng_pk = min(1024, w["ng"])
-    for name, call in (("power_spectrum", lambda: sim.power(ng_pk)), ("multipoles", lambda: sim.multipoles(ng_pk))):
+    fof_out = {}
+
+    def run_fof():
+        fof_out["halos"] = int(sim.fof(0.2, 100)[1].numel())
+
+    for name, call in (("power_spectrum", lambda: sim.power(ng_pk)), ("multipoles", lambda: sim.multipoles(ng_pk)),
+                       ("fof_halos", run_fof)):
         call()
         torch.cuda.synchronize()
         e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -632,7 +639,8 @@ def main():
             "step_roofline": {"B_ref_bytes": bref, "achieved_GBs": bref / (step_ms * 1e-3) / 1e9,
                               "frac": bref / (step_ms * 1e-3) / 1e9 / peak},
             "kernels": per_kernel,
-            "outputs_ms": {"ng_pk": ng_pk, **pk_ms},
+            "outputs_ms": {"ng_pk": ng_pk, **pk_ms, "fof_n_halos": fof_out.get("halos"),
+                           "fof_after_nodes": args.warmup + args.steps},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -267,6 +267,35 @@ int cola_ensemble_create(int32_t n, const cola_config* cfgs, const uint64_t* see
 int cola_ensemble_launch(cola_ensemble* e, void* stream);
 void cola_ensemble_destroy(cola_ensemble* e);
 
+/* Friends-of-friends halos (Sec. 2.1: FoF, linking length 0.2 of the mean
+ * inter-particle spacing; Sec. 2.4: halos of >= 100 particles with Warren
+ * masses M = m_p N (1 - N^-0.6)).  Positions are q + d nq / L in units of the
+ * mean spacing, periodic; two particles are friends when their minimum-image
+ * separation is at most b (decided in FP32, each operation rounded once);
+ * groups are the connected components.  Needs nq^3 < 2^31 and 0 < b < 1/2.
+ *
+ * cola_fof_workspace_size: bytes of the FoF workspace `fws` (device memory,
+ * caller-owned, about 24 bytes per particle; separate from the step's).
+ * cola_fof: group[p] (DEVICE int32[nq^3]) = the smallest particle index in
+ * p's group, from st->d (only d is read).  Deterministic.  Synchronises
+ * `stream` before returning, to report COLA_ENONFINITE (a non-finite position;
+ * that particle is left alone) or COLA_ETIMEOUT (a bounded union-find retry
+ * loop gave up).
+ * cola_fof_halos: the groups of at least min_members particles, ordered by
+ * root: halo_root[h], halo_size[h] (DEVICE int32 arrays with room for
+ * nq^3 / min_members entries) and *n_halos (DEVICE int64).  Uses fws.
+ * cola_mass_function: counts[i] (DEVICE int64[nbins]) = halos with
+ * log10(M / (Msun/h)) in [lo + i dlog, lo + (i+1) dlog), M the Warren mass
+ * with m_p = rho_c Omega_m (L / nq)^3, rho_c = 2.77536627e11 h^2 Msun Mpc^-3;
+ * reads the first min(*n_halos, max_halos) entries of halo_size. */
+int cola_fof_workspace_size(const cola_config* cfg, size_t* bytes);
+int cola_fof(const cola_config* cfg, const cola_state* st, double b, int32_t* group, void* fws, size_t fws_bytes,
+             void* stream);
+int cola_fof_halos(const cola_config* cfg, const int32_t* group, int32_t min_members, int32_t* halo_root,
+                   int32_t* halo_size, int64_t* n_halos, void* fws, size_t fws_bytes, void* stream);
+int cola_mass_function(const cola_config* cfg, const int32_t* halo_size, const int64_t* n_halos, int64_t max_halos,
+                       double log10m_lo, double dlog10m, int32_t nbins, int64_t* counts, void* stream);
+
 /* FFT tile autotuner: times the y pass of an n^3 mesh (device buffer of
  * n*n*2*cola_fft_pitch(n) floats, contents destroyed) for each admissible
  * column width and keeps the fastest for all later passes of that size in this

@@ -70,6 +70,11 @@ def _load():
         "cola_pm_force": ([cfgp, stp, dbl, vp, vp, sz, vp], ctypes.c_int),
         "cola_step": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
         "cola_step_host": ([cfgp, stp, stp, i32, vp, sz, vp], ctypes.c_int),
+        "cola_fof_workspace_size": ([cfgp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "cola_fof": ([cfgp, stp, ctypes.c_double, vp, vp, sz, vp], ctypes.c_int),
+        "cola_fof_halos": ([cfgp, vp, i32, vp, vp, vp, vp, sz, vp], ctypes.c_int),
+        "cola_mass_function": ([cfgp, vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, i32, vp, vp],
+                               ctypes.c_int),
         "cola_power_spectrum": ([cfgp, stp, i32, dbl, i32, i32, vp, vp, vp, i32, vp, sz, vp], ctypes.c_int),
         "cola_density": ([cfgp, stp, vp, vp, sz, vp], ctypes.c_int),
         "cola_step_table": ([cfgp, vp, vp, sz, vp], ctypes.c_int),
@@ -256,6 +261,29 @@ def cola_step_host(cfg, host: cola_state, dev: cola_state, step: int, ws, stream
     d and v copied back before return), dev the device state."""
     _check(LIB.cola_step_host(ctypes.byref(cfg), ctypes.byref(host), ctypes.byref(dev), step, _ptr(ws),
                               ws.numel() * ws.element_size(), _stream(stream)), "cola_step_host")
+
+
+def cola_fof_workspace_size(cfg) -> int:
+    out = ctypes.c_size_t(0)
+    _check(LIB.cola_fof_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "cola_fof_workspace_size")
+    return out.value
+
+
+def cola_fof(cfg, st: cola_state, b: float, group, fws, stream=None):
+    _check(LIB.cola_fof(ctypes.byref(cfg), ctypes.byref(st), b, _ptr(group), _ptr(fws),
+                        fws.numel() * fws.element_size(), _stream(stream)), "cola_fof")
+
+
+def cola_fof_halos(cfg, group, min_members: int, halo_root, halo_size, n_halos, fws, stream=None):
+    _check(LIB.cola_fof_halos(ctypes.byref(cfg), _ptr(group), min_members, _ptr(halo_root), _ptr(halo_size),
+                              _ptr(n_halos), _ptr(fws), fws.numel() * fws.element_size(), _stream(stream)),
+           "cola_fof_halos")
+
+
+def cola_mass_function(cfg, halo_size, n_halos, max_halos: int, lo: float, dlog: float, nbins: int, counts,
+                       stream=None):
+    _check(LIB.cola_mass_function(ctypes.byref(cfg), _ptr(halo_size), _ptr(n_halos), max_halos, lo, dlog, nbins,
+                                  _ptr(counts), _stream(stream)), "cola_mass_function")
 
 
 def cola_power_spectrum(cfg, st: cola_state, node: int, a_out: float, ng_pk: int, flags: int, k, pk, nmodes, ws,

@@ -1,0 +1,462 @@
+// Friends-of-friends halo finder (Sec. 2.1: FoF with a linking length of 0.2
+// of the mean inter-particle spacing; Sec. 2.4: halos of at least 100
+// particles, Warren et al. 2006 masses M = m_p N (1 - N^-0.6)) and the halo
+// mass function.
+//
+// Positions are taken in units of the mean spacing, u = q + d nq / L wrapped
+// into [0, nq), in FP32 with every operation rounded once (the __f*_rn
+// intrinsics are never contracted), so the friendship test r^2 <= b^2 gives
+// the same answer bit for bit wherever it is evaluated.
+//
+// Cell list: one cell per mean spacing (nq^3 cells, cell = floor(u); b < 1/2
+// keeps every friend in the 27 cells around a particle), built by counting
+// sort: a histogram, an exclusive scan, and a scatter of (u, p) into cell
+// order.
+//
+// Linking: one thread per particle, in cell order, visits the neighbour cells
+// its position can reach within b and tests their particles; a pair is taken
+// by the thread with the smaller sorted slot.  Friends are united in a
+// lock-free union-find whose roots only ever hook under smaller indices, so
+// every tree's root is its smallest member whatever order the unions land in:
+// the labels are deterministic.
+#include "cola_common.cuh"
+
+namespace cola {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kUnionCap = 1 << 20;  // bound on the retries of one find or union
+constexpr double kRhoCrit = 2.77536627e11;  // 3 H0^2 / (8 pi G) in h^2 Msun Mpc^-3
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct FofLayout {
+    size_t status, sorted, start, cursor, sums, total;
+};
+
+FofLayout fof_layout(long long np) {
+    FofLayout L;
+    size_t o = 0;
+    L.status = o;
+    o += 256;
+    L.sorted = o;
+    o = align256(o + (size_t)np * sizeof(float4));
+    L.start = o;
+    o = align256(o + (size_t)(np + 1) * sizeof(int));
+    L.cursor = o;
+    o = align256(o + (size_t)np * sizeof(int));
+    L.sums = o;
+    o = align256(o + (size_t)((np + 1 + kScanTile - 1) / kScanTile) * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+template <class T>
+T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+// position along one axis in units of the mean spacing, wrapped into [0, nq)
+__device__ __forceinline__ float wrap_pos(float q, float d, float inv, float nqf) {
+    float u = __fadd_rn(q, __fmul_rn(d, inv));
+    u = __fsub_rn(u, __fmul_rn(nqf, floorf(__fdiv_rn(u, nqf))));
+    if (u < 0.f) u = __fadd_rn(u, nqf);
+    if (u >= nqf) u = __fsub_rn(u, nqf);
+    return u;
+}
+
+// u of particle p and its cell; false (cell 0, u NaN) for non-finite input
+__device__ __forceinline__ bool particle_pos(const float* __restrict__ d, long long np, int nq, float inv, long long p,
+                                             float u[3], int* cell) {
+    const unsigned nqu = (unsigned)nq, pu = (unsigned)p;
+    const unsigned q[3] = {pu / (nqu * nqu), (pu / nqu) % nqu, pu % nqu};
+    const float nqf = (float)nq;
+    bool ok = true;
+    int c = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = wrap_pos((float)q[a], d[a * np + p], inv, nqf);
+        ok = ok && (u[a] >= 0.f && u[a] < nqf);  // false for NaN
+        int ca = (int)u[a];
+        if (ca > nq - 1) ca = nq - 1;
+        c = c * nq + ca;
+    }
+    if (!ok) {
+        u[0] = u[1] = u[2] = __int_as_float(0x7fc00000);
+        c = 0;
+    }
+    *cell = c;
+    return ok;
+}
+
+__global__ void k_fof_count(const float* __restrict__ d, long long np, int nq, float inv, int* count, int* status) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float u[3];
+    int c;
+    if (!particle_pos(d, np, nq, inv, p, u, &c)) set_status(status, COLA_ENONFINITE);
+    atomicAdd(count + c, 1);
+}
+
+__global__ void k_fof_scatter(const float* __restrict__ d, long long np, int nq, float inv, int* cursor,
+                              float4* sorted) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    float u[3];
+    int c;
+    particle_pos(d, np, nq, inv, p, u, &c);
+    const int slot = atomicAdd(cursor + c, 1);
+    sorted[slot] = make_float4(u[0], u[1], u[2], __int_as_float((int)p));
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of a[0..n) in place, a[n] = total (int32, n + 1 entries)
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of one value per thread; returns the block total
+__device__ __forceinline__ int block_exclusive_scan(int v, int* excl) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = w ? warp_tot[w - 1] : 0;
+    *excl = before + x - v;
+    const int total = warp_tot[kScanThreads / 32 - 1];
+    __syncthreads();  // warp_tot is reused by the next call
+    return total;
+}
+
+__device__ __forceinline__ void tile_load(const int* a, long long n, long long base, int v[kScanItems]) {
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const long long i = base + (long long)threadIdx.x * kScanItems + r;
+        v[r] = i < n ? a[i] : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* a, long long n, int* sums) {
+    int v[kScanItems];
+    tile_load(a, n, (long long)blockIdx.x * kScanTile, v);
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) s += v[r];
+    int ex;
+    const int tot = block_exclusive_scan(s, &ex);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// one block: exclusive scan of the nb tile sums in place; a[n] = total
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int* sums, int nb, int* a, long long n) {
+    int carry = 0;
+    for (long long base = 0; base < nb; base += kScanTile) {
+        int v[kScanItems];
+        tile_load(sums, nb, base, v);
+        int s = 0;
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) s += v[r];
+        int ex;
+        const int tot = block_exclusive_scan(s, &ex);
+        int run = carry + ex;
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) {
+            const long long i = base + (long long)threadIdx.x * kScanItems + r;
+            if (i < nb) sums[i] = run;
+            run += v[r];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) a[n] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int* a, long long n, const int* sums) {
+    const long long base = (long long)blockIdx.x * kScanTile;
+    int v[kScanItems];
+    tile_load(a, n, base, v);
+    int s = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) s += v[r];
+    int ex;
+    block_exclusive_scan(s, &ex);
+    int run = sums[blockIdx.x] + ex;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const long long i = base + (long long)threadIdx.x * kScanItems + r;
+        if (i < n) a[i] = run;
+        run += v[r];
+    }
+}
+
+int exclusive_scan(int* a, long long n, int* sums, cudaStream_t s) {
+    const int nb = (int)((n + kScanTile - 1) / kScanTile);
+    if (nb > 0) {
+        k_scan_tiles<<<nb, kScanThreads, 0, s>>>(a, n, sums);
+        if (int rc = check_launch()) return rc;
+    }
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, a, n);
+    if (int rc = check_launch()) return rc;
+    if (nb > 0) {
+        k_scan_apply<<<nb, kScanThreads, 0, s>>>(a, n, sums);
+        return check_launch();
+    }
+    return COLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// union-find over particle indices; parent[x] <= x always holds
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fof_find(int* parent, int x, int* status) {
+    for (int it = 0; it < kUnionCap; ++it) {
+        const int px = __ldcg(parent + x);
+        if (px == x) return x;
+        const int gp = __ldcg(parent + px);
+        if (gp != px) parent[x] = gp;  // path halving: gp is an ancestor of x, so gp <= px
+        x = gp;
+    }
+    set_status(status, COLA_ETIMEOUT);
+    return x;
+}
+
+__device__ __forceinline__ void fof_unite(int* parent, int a, int b, int* status) {
+    for (int it = 0; it < kUnionCap; ++it) {
+        a = fof_find(parent, a, status);
+        b = fof_find(parent, b, status);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(parent + b, b, a) == b) return;  // the larger root hooks under the smaller
+    }
+    set_status(status, COLA_ETIMEOUT);
+}
+
+__device__ __forceinline__ float min_image(float x, float nqf, float half) {
+    if (x > half) x = __fsub_rn(x, nqf);
+    if (x < -half) x = __fadd_rn(x, nqf);
+    return x;
+}
+
+__global__ void k_fof_init(int* parent, long long np) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) parent[p] = (int)p;
+}
+
+__global__ void k_fof_link(const float4* __restrict__ sorted, const int* __restrict__ start, long long np, int nq,
+                           float b2, float reach, int* parent, int* status) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const float4 a = sorted[k];
+    if (!(a.x == a.x && a.y == a.y && a.z == a.z)) return;  // non-finite input links to nothing
+    const float nqf = (float)nq, half = (float)(nq / 2.0);
+    const float pos[3] = {a.x, a.y, a.z};
+    int c[3], lo[3], hi[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        c[e] = (int)pos[e];
+        if (c[e] > nq - 1) c[e] = nq - 1;
+        const float f = pos[e] - (float)c[e];  // exact
+        lo[e] = f <= reach ? -1 : 0;
+        hi[e] = 1.f - f <= reach ? 1 : 0;
+    }
+    const int p = __float_as_int(a.w);
+    for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+        int cx = c[0] + ox;
+        cx = cx < 0 ? cx + nq : (cx >= nq ? cx - nq : cx);
+        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+            int cy = c[1] + oy;
+            cy = cy < 0 ? cy + nq : (cy >= nq ? cy - nq : cy);
+            for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+                int cz = c[2] + oz;
+                cz = cz < 0 ? cz + nq : (cz >= nq ? cz - nq : cz);
+                const int cell = (cx * nq + cy) * nq + cz;
+                const int j1 = start[cell + 1];
+                for (int j = start[cell] > k + 1 ? start[cell] : (int)k + 1; j < j1; ++j) {
+                    const float4 o = sorted[j];
+                    const float dx = min_image(__fsub_rn(a.x, o.x), nqf, half);
+                    const float dy = min_image(__fsub_rn(a.y, o.y), nqf, half);
+                    const float dz = min_image(__fsub_rn(a.z, o.z), nqf, half);
+                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    if (r2 <= b2) fof_unite(parent, p, __float_as_int(o.w), status);
+                }
+            }
+        }
+    }
+}
+
+// every label becomes its root, the smallest member of its group
+__global__ void k_fof_flatten(int* parent, long long np, int* status) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int x = (int)p;
+    for (int it = 0; it < kUnionCap; ++it) {
+        const int px = __ldcg(parent + x);
+        if (px == x) {
+            parent[p] = x;
+            return;
+        }
+        x = px;
+    }
+    set_status(status, COLA_ETIMEOUT);
+}
+
+__global__ void k_fof_sizes(const int* __restrict__ group, long long np, int* size) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) atomicAdd(size + group[p], 1);
+}
+
+__global__ void k_fof_flags(const int* __restrict__ group, const int* __restrict__ size, long long np, int nmin,
+                            int* flag) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) flag[p] = (group[p] == (int)p && size[p] >= nmin) ? 1 : 0;
+}
+
+// off: exclusive scan of the flags (np + 1 entries, off[np] = halo count)
+__global__ void k_fof_emit(const int* __restrict__ off, const int* __restrict__ size, long long np, int* halo_root,
+                           int* halo_size, long long* n_halos) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) *n_halos = off[np];
+    if (p >= np) return;
+    const int o = off[p];
+    if (off[p + 1] != o) {
+        halo_root[o] = (int)p;
+        halo_size[o] = size[p];
+    }
+}
+
+__global__ void k_mass_function(const int* __restrict__ halo_size, const long long* __restrict__ n_halos,
+                                long long max_halos, double m_p, double lo, double dlog, int nbins,
+                                unsigned long long* counts) {
+    const long long n = min(*n_halos, max_halos);
+    for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (long long)gridDim.x * blockDim.x) {
+        const double N = (double)halo_size[h];
+        const double lm = log10(m_p * N * (1.0 - pow(N, -0.6)));
+        const double t = floor((lm - lo) / dlog);
+        if (t >= 0.0 && t < (double)nbins) atomicAdd(counts + (int)t, 1ull);
+    }
+}
+
+unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int check_fof_args(const cola_config* cfg, long long* np) {
+    size_t ignored = 0;
+    if (!cfg) return COLA_EINVAL;
+    if (int rc = cola_workspace_size(cfg, &ignored)) return rc;
+    const long long n = (long long)cfg->nq * cfg->nq * cfg->nq;
+    if (n + 1 > 0x7fffffffll) return COLA_EUNSUPPORTED_SIZE;  // int32 particle indices and scans
+    *np = n;
+    return COLA_OK;
+}
+
+int read_status(const int* dev_status, cudaStream_t s) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, dev_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return COLA_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return COLA_ECUDA;
+    return h;
+}
+
+}  // namespace
+}  // namespace cola
+
+extern "C" {
+
+int cola_fof_workspace_size(const cola_config* cfg, size_t* bytes) {
+    long long np = 0;
+    if (!bytes) return COLA_EINVAL;
+    if (int rc = cola::check_fof_args(cfg, &np)) return rc;
+    *bytes = cola::fof_layout(np).total;
+    return COLA_OK;
+}
+
+int cola_fof(const cola_config* cfg, const cola_state* st, double b, int32_t* group, void* fws, size_t fws_bytes,
+             void* stream) {
+    using namespace cola;
+    long long np = 0;
+    if (int rc = check_fof_args(cfg, &np)) return rc;
+    if (!st || !st->d || !group || !fws || !(b > 0.0 && b < 0.5)) return COLA_EINVAL;
+    const FofLayout L = fof_layout(np);
+    if (fws_bytes < L.total) return COLA_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* status = at<int>(fws, L.status);
+    int* start = at<int>(fws, L.start);
+    int* cursor = at<int>(fws, L.cursor);
+    float4* sorted = at<float4>(fws, L.sorted);
+    const float inv = (float)((double)cfg->nq / cfg->box);
+    const int T = 256;
+    const unsigned nb = blocks_for(np, T);
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(start, 0, (size_t)(np + 1) * sizeof(int), s) != cudaSuccess)
+        return COLA_ECUDA;
+    k_fof_count<<<nb, T, 0, s>>>(st->d, np, cfg->nq, inv, start, status);
+    if (int rc = check_launch()) return rc;
+    if (int rc = exclusive_scan(start, np, at<int>(fws, L.sums), s)) return rc;
+    if (cudaMemcpyAsync(cursor, start, (size_t)np * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return COLA_ECUDA;
+    k_fof_scatter<<<nb, T, 0, s>>>(st->d, np, cfg->nq, inv, cursor, sorted);
+    k_fof_init<<<nb, T, 0, s>>>(group, np);
+    // cells wider than the linking length by a margin far above FP32 rounding
+    k_fof_link<<<nb, T, 0, s>>>(sorted, start, np, cfg->nq, (float)(b * b), (float)b + 0.01f, group, status);
+    k_fof_flatten<<<nb, T, 0, s>>>(group, np, status);
+    if (int rc = check_launch()) return rc;
+    return read_status(status, s);
+}
+
+int cola_fof_halos(const cola_config* cfg, const int32_t* group, int32_t min_members, int32_t* halo_root,
+                   int32_t* halo_size, int64_t* n_halos, void* fws, size_t fws_bytes, void* stream) {
+    using namespace cola;
+    long long np = 0;
+    if (int rc = check_fof_args(cfg, &np)) return rc;
+    if (!group || !halo_root || !halo_size || !n_halos || !fws || min_members < 1) return COLA_EINVAL;
+    const FofLayout L = fof_layout(np);
+    if (fws_bytes < L.total) return COLA_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int* size = at<int>(fws, L.cursor);
+    int* off = at<int>(fws, L.start);
+    const int T = 256;
+    const unsigned nb = blocks_for(np, T);
+    if (cudaMemsetAsync(size, 0, (size_t)np * sizeof(int), s) != cudaSuccess) return COLA_ECUDA;
+    k_fof_sizes<<<nb, T, 0, s>>>(group, np, size);
+    k_fof_flags<<<nb, T, 0, s>>>(group, size, np, min_members, off);
+    if (int rc = check_launch()) return rc;
+    if (int rc = exclusive_scan(off, np, at<int>(fws, L.sums), s)) return rc;
+    k_fof_emit<<<nb, T, 0, s>>>(off, size, np, halo_root, halo_size, reinterpret_cast<long long*>(n_halos));
+    return check_launch();
+}
+
+int cola_mass_function(const cola_config* cfg, const int32_t* halo_size, const int64_t* n_halos, int64_t max_halos,
+                       double log10m_lo, double dlog10m, int32_t nbins, int64_t* counts, void* stream) {
+    using namespace cola;
+    long long np = 0;
+    if (int rc = check_fof_args(cfg, &np)) return rc;
+    if (!halo_size || !n_halos || !counts || max_halos < 0 || nbins < 1 || !(dlog10m > 0.0)) return COLA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(counts, 0, (size_t)nbins * sizeof(int64_t), s) != cudaSuccess) return COLA_ECUDA;
+    if (max_halos == 0) return COLA_OK;
+    const double m_p = kRhoCrit * cfg->cosmo.omega_m * std::pow(cfg->box / cfg->nq, 3);
+    const int T = 256;
+    long long blocks = (max_halos + T - 1) / T;
+    if (blocks > 4096) blocks = 4096;
+    k_mass_function<<<(unsigned)blocks, T, 0, s>>>(halo_size, reinterpret_cast<const long long*>(n_halos), max_halos,
+                                                   m_p, log10m_lo, dlog10m, nbins,
+                                                   reinterpret_cast<unsigned long long*>(counts));
+    return check_launch();
+}
+
+}  // extern "C"

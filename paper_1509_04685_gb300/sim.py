@@ -42,6 +42,29 @@ class Simulation:
         L.cola_step_host(self.cfg, host, self.state, j, self.ws, self.stream)
         self.node = min(j + 1, self.cfg.n_steps - 1)
 
+    def fof(self, b: float = 0.2, min_members: int = 100):
+        """Friends-of-friends groups of the current positions: (group label of
+        every particle, halo roots, halo sizes) as device tensors, halos of at
+        least min_members particles ordered by root."""
+        if getattr(self, "fws", None) is None:
+            self.fws = torch.empty(L.cola_fof_workspace_size(self.cfg), dtype=torch.uint8, device=self.device)
+        group = torch.empty(self.np, dtype=torch.int32, device=self.device)
+        L.cola_fof(self.cfg, self.state, b, group, self.fws, self.stream)
+        cap = self.np // max(1, min_members) + 1
+        roots = torch.empty(cap, dtype=torch.int32, device=self.device)
+        sizes = torch.empty(cap, dtype=torch.int32, device=self.device)
+        n = torch.zeros(1, dtype=torch.int64, device=self.device)
+        L.cola_fof_halos(self.cfg, group, min_members, roots, sizes, n, self.fws, self.stream)
+        nh = int(n.item())
+        return group, roots[:nh], sizes[:nh]
+
+    def mass_function(self, sizes, lo: float, dlog: float, nbins: int):
+        """Halo counts per bin of log10 M (Warren masses) for halo sizes `sizes`."""
+        n = torch.tensor([sizes.numel()], dtype=torch.int64, device=self.device)
+        counts = torch.empty(nbins, dtype=torch.int64, device=self.device)
+        L.cola_mass_function(self.cfg, sizes, n, sizes.numel(), lo, dlog, nbins, counts, self.stream)
+        return counts
+
     def run(self, steps=None):
         for j in range(self.cfg.n_steps) if steps is None else steps:
             self.step(j)

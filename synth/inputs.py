@@ -5,7 +5,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["random_displacements", "random_state", "plane_wave_psi1", "crossed_waves_delta",
-           "random_mesh", "single_mode_delta"]
+           "random_mesh", "single_mode_delta", "clumpy_displacements"]
 
 
 def random_displacements(seed: int, nq: int, rms: float) -> np.ndarray:
@@ -50,3 +50,18 @@ def single_mode_delta(n: int, L: float, eps: float, nvec) -> np.ndarray:
 def random_mesh(seed: int, shape, scale: float = 1.0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return (rng.standard_normal(shape) * scale).astype(np.float32)
+
+
+def clumpy_displacements(seed: int, nq: int, L: float, nclump: int, spread: float, frac: float = 0.7) -> np.ndarray:
+    """Displacements (3, nq^3) that move a fraction `frac` of the particles into
+    nclump Gaussian clumps of rms `spread` (in mean spacings) around uniform
+    random centres; the rest stay within 0.05 spacings of their lattice sites."""
+    rng = np.random.default_rng(seed)
+    p = np.arange(nq**3, dtype=np.int64)
+    q = np.stack([p // (nq * nq), (p // nq) % nq, p % nq]).astype(np.float64)
+    centres = rng.uniform(0, nq, (nclump, 3))
+    target = q + rng.normal(0.0, 0.05, q.shape)
+    moved = rng.uniform(size=nq**3) < frac
+    which = rng.integers(0, nclump, moved.sum())
+    target[:, moved] = centres[which].T + rng.normal(0.0, spread, (3, moved.sum()))
+    return ((target - q) * (L / nq)).astype(np.float32)

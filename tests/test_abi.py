@@ -69,3 +69,21 @@ def test_particle_set_traversal_validates_its_arguments():
         assert C.LIB.cola_particle_set_traversal(edge, bk) == -1
     for edge, bk in ((32, 8), (128, 16), (4096, 32), (256, 256), (0, 0)):  # 0 restores the default
         assert C.LIB.cola_particle_set_traversal(edge, bk) == 0
+
+
+def test_fof_entry_points_validate_before_launching():
+    import paper_1509_04685_gb300 as C
+    L = C.LIB
+    cfg = C.make_config(16, 48, 64.0, 0.05)
+    fsize = C.cola_fof_workspace_size(cfg)
+    assert fsize > 16**3 * 24
+    fake = 1 << 40
+    st = C.cola_state(fake, fake, fake, fake)
+    call = lambda b, g, ws, n: L.cola_fof(ctypes.byref(cfg), ctypes.byref(st), b, g, ws, n, None)
+    assert call(0.5, fake, fake, fsize) == -1
+    assert call(0.0, fake, fake, fsize) == -1
+    assert call(0.2, None, fake, fsize) == -1
+    assert call(0.2, fake, fake, fsize - 1) == -2
+    assert L.cola_fof_halos(ctypes.byref(cfg), fake, 0, fake, fake, fake, fake, fsize, None) == -1
+    assert L.cola_mass_function(ctypes.byref(cfg), fake, fake, 10, 12.0, 0.0, 5, fake, None) == -1
+    assert C.cola_launch_count() == 0
