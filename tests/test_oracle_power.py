@@ -121,3 +121,50 @@ def test_small_amplitude_zeldovich_field_obeys_kaiser():
     sel = (k < 0.25 * np.pi * ng / L) & (nm > 50)
     np.testing.assert_allclose(p0[sel], e0[sel], rtol=5e-3)
     np.testing.assert_allclose(p2[sel], e2[sel], rtol=2e-2)
+
+
+def _field_with_raw_power(ng, L, praw):
+    """A real field whose half-spectrum has |delta_k|^2 L^3 / ng^6 = praw (zero phases)."""
+    return np.fft.irfftn(np.sqrt(praw * ng**6 / L**3), s=(ng, ng, ng), axes=(0, 1, 2))
+
+
+def test_jing_image_sum_reduces_to_the_closed_form():
+    # with n_eff = 0 the image sum of W^2 is Jing's closed form prod [1 - 2/3 sin^2(pi n_i / ng)],
+    # up to the truncated tails: per axis and side at most int_J^inf dn / (pi n)^4 = 1 / (3 pi^4 J^3)
+    ng, J = 16, 8
+    nx, ny, nz = power._modes(ng)
+    C = power.jing_alias_sum(nx, ny, nz, ng, 0.0, images=J)
+    s = lambda t: np.sin(np.pi * t / ng) ** 2
+    np.testing.assert_allclose(C, (1 - 2 / 3 * s(nx)) * (1 - 2 / 3 * s(ny)) * (1 - 2 / 3 * s(nz)),
+                               atol=6 / (3 * np.pi**4 * J**3))
+    # the n = 0 image alone is the CIC window squared
+    C0 = power.jing_alias_sum(nx, ny, nz, ng, 1.7, images=0)
+    W = (np.sinc(nx / ng) * np.sinc(ny / ng) * np.sinc(nz / ng)) ** 2
+    np.testing.assert_allclose(C0, W**2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("index,tol", [(-2.5, 5e-3), (-1.5, 1e-2)])
+def test_jing_iteration_recovers_an_aliased_power_law(index, tol):
+    # raw power built with ten images of a power law: the iterated estimate (two
+    # images, slopes from the data) recovers the mode-averaged true power in every
+    # bin, where the closed-form division is far off near the Nyquist frequency
+    ng, L = 32, 100.0
+    nx, ny, nz = power._modes(ng)
+    m2 = (nx**2 + ny**2 + nz**2).astype(np.float64)
+    kf = 2 * np.pi / L
+    P = np.where(m2 > 0, (kf * np.sqrt(np.where(m2 > 0, m2, 1.0))) ** index, 0.0)
+    raw = power.jing_alias_sum(nx, ny, nz, ng, index, images=10) * P
+    delta = _field_with_raw_power(ng, L, raw)
+    _, p_true, _ = power.power_from_delta(_field_with_raw_power(ng, L, P), L)
+    k, p, nm = power.power_jing_iterative(delta, L)
+    assert np.abs(p / p_true - 1).max() < tol
+    _, pc, _ = power.power_from_delta(delta, L, power.DECONV_CIC | power.ALIAS_JING)
+    assert np.abs(pc[-1] / p_true[-1] - 1) > 1.0
+
+
+def test_local_slopes_of_a_power_law():
+    k = np.geomspace(0.1, 2.0, 12)
+    np.testing.assert_allclose(power.local_slopes(k, 3.0 * k**-1.7), -1.7, rtol=1e-12)
+    s = power.local_slopes(k, 3.0 * k**-9.0)
+    assert np.all(s == -power.NEFF_CLAMP)
+    assert power.local_slopes(k[:1], k[:1])[0] == 0.0
