@@ -588,6 +588,7 @@ def main():
         fof_out["halos"] = int(sim.fof(0.2, 100)[1].numel())
 
     for name, call in (("power_spectrum", lambda: sim.power(ng_pk)), ("multipoles", lambda: sim.multipoles(ng_pk)),
+                       ("power_spectrum_jing_iterated", lambda: sim.power(ng_pk, flags=C.PK_ALIAS_ITER)),
                        ("fof_halos", run_fof)):
         call()
         torch.cuda.synchronize()

@@ -55,6 +55,12 @@ extern "C" {
 
 #define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.4) */
 #define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.4) */
+/* The full Jing (2005) correction, iterated (Sec. 2.4): divide each mode by
+ * C(m) = sum over images |n_i| <= 2 of W_CIC^2(m + ng n) (|m + ng n|/|m|)^n_eff,
+ * n_eff per bin the log-slope of the previous estimate between neighbouring
+ * bins (clamped to [-4, 4]); start from flags 1 | 2, three iterations.  Use
+ * alone (not with 1 or 2), and with cola_power_spectrum only. */
+#define COLA_PK_ALIAS_ITER 4
 
 /* Flat LCDM parameters (Sec. 2.1, MICE-GC: 0.25, 0.75, 0.044, 0.7, 0.8, 0.95). */
 typedef struct cola_cosmology {

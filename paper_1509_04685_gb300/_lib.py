@@ -24,7 +24,7 @@ NET_NPARAMS = 9971
 NET_NPACK = 31104
 NET_OFFSETS = {"W1": (0, (16, 4, 27)), "b1": (1728, (16,)), "W2": (1744, (16, 16, 27)), "b2": (8656, (16,)),
                "W3": (8672, (3, 16, 27)), "b3": (9968, (3,))}
-PK_DECONV_CIC, PK_ALIAS_JING = 1, 2
+PK_DECONV_CIC, PK_ALIAS_JING, PK_ALIAS_ITER = 1, 2, 4
 TABLE_COLUMNS = ("a", "green", "c1", "c2", "kick", "drift", "dD1", "dD2", "D1", "D2", "dD1da", "dD2da")
 
 

@@ -251,7 +251,8 @@ static int power_common(const cola_config* cfg, const cola_state* st, int32_t no
     const bool rsd = p2 && p4;
     if (!state_ok(st, rsd) || !k || !pk || !nmodes) return COLA_EINVAL;
     if (!mesh_ok(ng_pk) || ng_pk > cfg->ng) return COLA_EUNSUPPORTED_SIZE;
-    if (nbins != ng_pk / 2 || node < 0 || node >= cfg->n_steps || (flags & ~3)) return COLA_EINVAL;
+    if (nbins != ng_pk / 2 || node < 0 || node >= cfg->n_steps || (flags & ~7)) return COLA_EINVAL;
+    if ((flags & COLA_PK_ALIAS_ITER) && ((flags & 3) || rsd)) return COLA_EINVAL;
     const double a_node = host_node_a(cfg, node);
     const double* snap = nullptr;
     if (rsd || std::fabs(a_out - a_node) > 1e-12 * a_node) {

@@ -1,6 +1,6 @@
 // Matter power spectrum shells (Sec. 2.4): P(k) = <|delta_k|^2> over the modes
 // of each k-bin, with optional CIC deconvolution and the Jing (2005) CIC
-// aliasing correction.
+// aliasing correction, closed form or iterated.
 //
 // Bin i (1 .. ng/2) holds the modes with (i - 1/2)^2 < |n|^2 < (i + 1/2)^2,
 // decided in integer arithmetic.  Half-spectrum modes count twice except on
@@ -17,9 +17,60 @@ namespace cola {
 constexpr int kPkBlocks = 608;  // 4 blocks per SM on a 152-SM GB300
 constexpr int kPkThreads = 256;
 
+// Iterated Jing (2005) correction of one mode m (flag COLA_PK_ALIAS_ITER): the
+// raw power over C(m) = sum over the images |n_i| <= kJingImages of
+// W^2(m + ng n) (|m + ng n| / |m|)^n_eff, W the CIC window, P taken as a power
+// law of index n_eff (this mode's bin) around |m|.  sin(pi (m + ng n) / ng) =
+// +-sin(pi m / ng), so each image's window factor is, per axis,
+// sin^4(pi m / ng) / (pi (m + ng n) / ng)^4 (1 for m = n = 0, 0 for m = 0 != n).
+constexpr int kJingImages = 2;
+constexpr int kJingIterations = 3;
+constexpr double kNeffClamp = 4.0;
+
+__device__ __forceinline__ float jing_alias_sum(const int nn[3], int ng, float n_eff) {
+    constexpr int NI = 2 * kJingImages + 1;
+    const float inv_ng = 1.0f / (float)ng;
+    float fa[3][NI], x[3][NI];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float s = sinpif((float)nn[a] * inv_ng);
+        const float s4 = (s * s) * (s * s);
+#pragma unroll
+        for (int j = 0; j < NI; ++j) {
+            const int n = j - kJingImages;
+            x[a][j] = (float)(nn[a] + ng * n);
+            if (nn[a] == 0) {
+                fa[a][j] = n == 0 ? 1.f : 0.f;
+            } else {
+                const float t = 3.14159265358979f * x[a][j] * inv_ng;
+                fa[a][j] = s4 / ((t * t) * (t * t));
+            }
+        }
+    }
+    const float lm2 = log2f((float)((long long)nn[0] * nn[0] + (long long)nn[1] * nn[1] + (long long)nn[2] * nn[2]));
+    const float h = 0.5f * n_eff;
+    float C = 0.f;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        if (fa[0][i] == 0.f) continue;
+#pragma unroll
+        for (int j = 0; j < NI; ++j) {
+            const float wxy = fa[0][i] * fa[1][j];
+            if (wxy == 0.f) continue;
+            const float rxy = x[0][i] * x[0][i] + x[1][j] * x[1][j];
+#pragma unroll
+            for (int l = 0; l < NI; ++l) {
+                const float w = wxy * fa[2][l];
+                if (w != 0.f) C += w * exp2f(h * (log2f(rxy + x[2][l] * x[2][l]) - lm2));
+            }
+        }
+    }
+    return C;
+}
+
 template <bool MULTI>
 __global__ void k_pk_shells(const float2* __restrict__ mk, int ng, long long P, float amp_scale, float kf, int flags,
-                            int nbins, double* __restrict__ part) {
+                            int nbins, double* __restrict__ part, const double* __restrict__ neff) {
     constexpr int NA = MULTI ? 5 : 3;  // sum w, sum w k, sum w P [, sum w P L2, sum w P L4]
     extern __shared__ float bins[];
     for (int i = threadIdx.x; i < NA * nbins; i += blockDim.x) bins[i] = 0.f;
@@ -44,6 +95,10 @@ __global__ void k_pk_shells(const float2* __restrict__ mk, int ng, long long P, 
         const float2 d = mk[row * P + kz];
         const float dr = d.x * amp_scale, di = d.y * amp_scale;
         float p = dr * dr + di * di;
+        if (flags & COLA_PK_ALIAS_ITER) {
+            const int nn[3] = {nx, ny, kz};
+            p /= jing_alias_sum(nn, ng, (float)neff[i - 1]);
+        }
         if (flags & COLA_PK_DECONV_CIC) {
             float W = 1.f;
             const int nn[3] = {nx, ny, kz};
@@ -110,8 +165,48 @@ __global__ void k_pk_reduce(const double* __restrict__ part, int nblocks, int nb
     }
 }
 
+// n_eff per bin for the next Jing iteration: d ln P / d ln k over the
+// neighbouring bins (one-sided at the ends; 0 where a power is not positive),
+// clamped to [-kNeffClamp, kNeffClamp]
+__global__ void k_pk_slopes(const double* __restrict__ k, const double* __restrict__ pk, int nbins, double* neff) {
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const int lo = b > 0 ? b - 1 : 0, hi = b + 1 < nbins ? b + 1 : nbins - 1;
+        double n = 0.0;
+        if (hi != lo && pk[lo] > 0.0 && pk[hi] > 0.0 && k[hi] > k[lo] && k[lo] > 0.0)
+            n = fmin(fmax(log(pk[hi] / pk[lo]) / log(k[hi] / k[lo]), -kNeffClamp), kNeffClamp);
+        neff[b] = n;
+    }
+}
+
 int launch_power(const float2* mk, int ng, long long rs, double box, int flags, double* part, double* k, double* pk,
                  double* nmodes, int nbins, cudaStream_t s, double* p2, double* p4) {
+    if (flags & COLA_PK_ALIAS_ITER) {
+        // closed-form start, then kJingIterations passes with slopes from the last estimate
+        int rc = launch_power(mk, ng, rs, box, COLA_PK_DECONV_CIC | COLA_PK_ALIAS_JING, part, k, pk, nmodes, nbins, s,
+                              nullptr, nullptr);
+        double* neff = part + (size_t)kPkBlocks * 5 * nbins;
+        for (int it = 0; it < kJingIterations && !rc; ++it) {
+            k_pk_slopes<<<1, 256, 0, s>>>(k, pk, nbins, neff);
+            if ((rc = check_launch())) break;
+            const double ng3 = (double)ng * ng * ng;
+            const float amp_scale = (float)(box * sqrt(box) / ng3);
+            const float kf = (float)(2.0 * 3.14159265358979323846 / box);
+            const size_t smem = (size_t)3 * nbins * sizeof(float);
+            if (smem > 48 * 1024 && cudaFuncSetAttribute(k_pk_shells<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)smem) != cudaSuccess)
+                return COLA_ECUDA;
+            {
+                ProfScope ps(kKPkShells, s);
+                k_pk_shells<false><<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, COLA_PK_ALIAS_ITER,
+                                                                     nbins, part, neff);
+            }
+            if ((rc = check_launch())) break;
+            ProfScope ps(kKPkReduce, s);
+            k_pk_reduce<<<(nbins + 127) / 128, 128, 0, s>>>(part, kPkBlocks, nbins, k, pk, nmodes, nullptr, nullptr);
+            rc = check_launch();
+        }
+        return rc;
+    }
     const double ng3 = (double)ng * ng * ng;
     const float amp_scale = (float)(box * sqrt(box) / ng3);  // sqrt(L^3 / ng^6)
     const float kf = (float)(2.0 * 3.14159265358979323846 / box);
@@ -123,7 +218,7 @@ int launch_power(const float2* mk, int ng, long long rs, double box, int flags, 
         return COLA_ECUDA;
     {
         ProfScope ps(kKPkShells, s);
-        kern<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, flags, nbins, part);
+        kern<<<kPkBlocks, kPkThreads, smem, s>>>(mk, ng, rs, amp_scale, kf, flags, nbins, part, nullptr);
     }
     int rc = check_launch();
     if (rc) return rc;
@@ -133,6 +228,7 @@ int launch_power(const float2* mk, int ng, long long rs, double box, int flags, 
     return check_launch();
 }
 
-size_t power_partial_bytes(int nbins) { return (size_t)kPkBlocks * 5 * nbins * sizeof(double); }
+// per-block partial sums, then the n_eff table of the iterated Jing correction
+size_t power_partial_bytes(int nbins) { return ((size_t)kPkBlocks * 5 + 1) * nbins * sizeof(double); }
 
 }  // namespace cola

@@ -59,6 +59,11 @@ def test_entry_points_reject_bad_arguments_without_launching():
     assert L.cola_step_host(ctypes.byref(cfg), ctypes.byref(hs), ctypes.byref(st), 40, fake, size, None) == -1
     assert L.cola_step_host(ctypes.byref(cfg), ctypes.byref(hs), ctypes.byref(st), 0, fake, size - 1, None) == -2
     assert L.cola_step_host(ctypes.byref(cfg), None, ctypes.byref(st), 0, fake, size, None) == -1
+    for flags in (4 | 1, 4 | 2, 8):
+        assert L.cola_power_spectrum(ctypes.byref(cfg), ctypes.byref(st), 0, 0.05, 24, flags, fake, fake, fake, 12,
+                                     fake, size, None) == -1
+    assert L.cola_power_multipoles(ctypes.byref(cfg), ctypes.byref(st), 0, 0.05, 24, 4, fake, fake, fake, fake, fake,
+                                   12, fake, size, None) == -1
     assert C.cola_launch_count() == 0
     assert C.cola_strerror(-6).startswith("non-finite")
 
