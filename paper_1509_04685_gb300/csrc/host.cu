@@ -5,8 +5,8 @@
 // and the fused gather + kick + drift waits for them.  The updated positions
 // and velocities then come back on the caller's stream, and the call returns
 // once they have landed.  Pinned host memory makes the copies asynchronous DMA
-// at the link's rate; pageable memory works too, at the speed of the driver's
-// staging.
+// at the link's rate; pageable memory works too, through CUDA's own staging
+// copies.
 #include "cola_common.cuh"
 
 namespace {
