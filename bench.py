@@ -379,15 +379,15 @@ def csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources and on this workload (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
-    if j.get("csrc_digest") != csrc_digest():
+    if j.get("csrc_digest") != csrc_digest() or j.get("workload") != workload:
         return None
     k = j.get("kernels", {}).get(kernel)
     return None if k is None else float(k["dram_bytes_per_launch_full"])
@@ -636,7 +636,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": ke},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
-                         "algorithmic_bytes_per_launch": alg, "traffic": ncu_traffic(dom)},
+                         "algorithmic_bytes_per_launch": alg, "traffic": ncu_traffic(dom, w["name"])},
             "step_roofline": {"B_ref_bytes": bref, "achieved_GBs": bref / (step_ms * 1e-3) / 1e9,
                               "frac": bref / (step_ms * 1e-3) / 1e9 / peak},
             "kernels": per_kernel,
