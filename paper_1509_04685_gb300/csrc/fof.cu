@@ -259,43 +259,72 @@ __global__ void k_fof_init(int* parent, long long np) {
     if (p < np) parent[p] = (int)p;
 }
 
+// A friend pair (k, j), k < j in sorted order, is taken by thread k.  Thread
+// k's candidate cells are the neighbour cells its position reaches within
+// `reach`; any superset also works (the distance test decides).  When all 32
+// lanes of a warp lie in one cell (the dense regions, where the work is), the
+// warp walks the union of its lanes' cells in step: every lane reads the same
+// candidate (one broadcast load) and the loop bounds are the same for all.
+__device__ __forceinline__ int wrap_cell(int c, int nq) { return c < 0 ? c + nq : (c >= nq ? c - nq : c); }
+
+__device__ __forceinline__ void link_candidate(const float4& a, const float4& o, float nqf, float half, float b2,
+                                               int* parent, int* status) {
+    const float dx = min_image(__fsub_rn(a.x, o.x), nqf, half);
+    const float dy = min_image(__fsub_rn(a.y, o.y), nqf, half);
+    const float dz = min_image(__fsub_rn(a.z, o.z), nqf, half);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    if (r2 <= b2) fof_unite(parent, __float_as_int(a.w), __float_as_int(o.w), status);
+}
+
 __global__ void k_fof_link(const float4* __restrict__ sorted, const int* __restrict__ start, long long np, int nq,
                            float b2, float reach, int* parent, int* status) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const float4 a = sorted[k];
-    if (!(a.x == a.x && a.y == a.y && a.z == a.z)) return;  // non-finite input links to nothing
+    const bool active = k < np;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) a = sorted[k];
+    const bool finite = active && a.x == a.x && a.y == a.y && a.z == a.z;  // non-finite input links to nothing
     const float nqf = (float)nq, half = (float)(nq / 2.0);
     const float pos[3] = {a.x, a.y, a.z};
     int c[3], lo[3], hi[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        c[e] = (int)pos[e];
+        c[e] = finite ? (int)pos[e] : 0;
         if (c[e] > nq - 1) c[e] = nq - 1;
         const float f = pos[e] - (float)c[e];  // exact
         lo[e] = f <= reach ? -1 : 0;
         hi[e] = 1.f - f <= reach ? 1 : 0;
     }
-    const int p = __float_as_int(a.w);
+    const int cid = finite ? (c[0] * nq + c[1]) * nq + c[2] : -1;
+    const unsigned full = 0xffffffffu;
+    const int cid0 = __shfl_sync(full, cid, 0);
+    if (__all_sync(full, cid == cid0 && cid >= 0)) {
+        unsigned mine = 0;  // this lane's cells as bits o = (ox + 1) 9 + (oy + 1) 3 + (oz + 1)
+        for (int ox = lo[0]; ox <= hi[0]; ++ox)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int oz = lo[2]; oz <= hi[2]; ++oz) mine |= 1u << ((ox + 1) * 9 + (oy + 1) * 3 + (oz + 1));
+        const unsigned cells = __reduce_or_sync(full, mine);
+        for (int o = 0; o < 27; ++o) {
+            if (!((cells >> o) & 1u)) continue;
+            const int cell = (wrap_cell(c[0] + o / 9 - 1, nq) * nq + wrap_cell(c[1] + (o / 3) % 3 - 1, nq)) * nq +
+                             wrap_cell(c[2] + o % 3 - 1, nq);
+            const int j1 = start[cell + 1];
+            for (int j = start[cell]; j < j1; ++j) {
+                const float4 q = sorted[j];
+                if (j > k) link_candidate(a, q, nqf, half, b2, parent, status);
+            }
+        }
+        return;
+    }
+    if (!finite) return;
     for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-        int cx = c[0] + ox;
-        cx = cx < 0 ? cx + nq : (cx >= nq ? cx - nq : cx);
+        const int cx = wrap_cell(c[0] + ox, nq);
         for (int oy = lo[1]; oy <= hi[1]; ++oy) {
-            int cy = c[1] + oy;
-            cy = cy < 0 ? cy + nq : (cy >= nq ? cy - nq : cy);
+            const int cy = wrap_cell(c[1] + oy, nq);
             for (int oz = lo[2]; oz <= hi[2]; ++oz) {
-                int cz = c[2] + oz;
-                cz = cz < 0 ? cz + nq : (cz >= nq ? cz - nq : cz);
-                const int cell = (cx * nq + cy) * nq + cz;
+                const int cell = (cx * nq + cy) * nq + wrap_cell(c[2] + oz, nq);
                 const int j1 = start[cell + 1];
-                for (int j = start[cell] > k + 1 ? start[cell] : (int)k + 1; j < j1; ++j) {
-                    const float4 o = sorted[j];
-                    const float dx = min_image(__fsub_rn(a.x, o.x), nqf, half);
-                    const float dy = min_image(__fsub_rn(a.y, o.y), nqf, half);
-                    const float dz = min_image(__fsub_rn(a.z, o.z), nqf, half);
-                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    if (r2 <= b2) fof_unite(parent, p, __float_as_int(o.w), status);
-                }
+                for (int j = start[cell] > k + 1 ? start[cell] : (int)k + 1; j < j1; ++j)
+                    link_candidate(a, sorted[j], nqf, half, b2, parent, status);
             }
         }
     }
