@@ -1,5 +1,6 @@
 """Pins of oracle/fof.py: friends-of-friends groups, Warren masses, mass function."""
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -122,12 +123,24 @@ def test_labels_are_smallest_member_indices():
     np.testing.assert_array_equal(g[g], g)
 
 
+def _golden_masses():
+    rows = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_halo_masses.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[f[0]] = [float(x) for x in f[1:]]
+    return rows
+
+
 def test_particle_mass_and_warren_masses():
-    # Sec. 2.1: MICE-GC (Omega_m = 0.25, 4096^3 particles in 3072 Mpc/h) has m_p = 2.93e10 Msun/h
-    mp = fof.particle_mass(0.25, 3072.0, 4096)
-    assert mp == pytest.approx(2.93e10, rel=2e-3)
-    # Sec. 2.4: 100 particles correspond to about 10^12.5 Msun/h at that resolution
-    assert np.log10(fof.warren_mass(100, mp)) == pytest.approx(12.5, abs=0.1)
+    g = _golden_masses()
+    # Sec. 2.1: the MICE-GC particle mass; Sec. 2.4: the mass of the smallest kept halos
+    om, L, n, value, tol = g["particle_mass"]
+    mp = fof.particle_mass(om, L, int(n))
+    assert mp == pytest.approx(value, rel=tol)
+    om, L, n, members, value, tol = g["min_halo_log10_mass"]
+    assert np.log10(fof.warren_mass(members, fof.particle_mass(om, L, int(n)))) == pytest.approx(value, abs=tol)
     # the correction removes one particle's worth at N = 1 and vanishes for large N
     assert fof.warren_mass(1, mp) == 0.0
     assert fof.warren_mass(1e8, mp) / (1e8 * mp) == pytest.approx(1.0, abs=2e-5)
