@@ -1,5 +1,5 @@
-"""Friends-of-friends halo finder and halo mass function (Sec. 2.1: FoF
-(Davis et al. 1985) with a linking length of 0.2; Sec. 2.4: halos of at least
+"""Friends-of-friends halo finder and halo mass function (Sec. 2.1: FoF of
+Davis et al. 1985, linking length b = 0.2; Sec. 2.4: halos of at least
 100 particles, masses with the Warren et al. 2006 correction
 M = m_p N (1 - N^-0.6)).
 
