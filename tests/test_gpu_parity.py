@@ -160,6 +160,28 @@ def test_particle_traversal_tiles_give_identical_results(nq, ng):
     assert sim.status() == 0
 
 
+def test_density_with_every_particle_on_one_point():
+    # the degenerate deposit: 32^3 particles on one point fill the eight cells around
+    # it with fixed-point sums of up to 2^40 x 2^15 each (no uint64 overflow)
+    nq, ng, L = 32, 96, 128.0
+    p = np.arange(nq**3)
+    q = np.stack([p // (nq * nq), (p // nq) % nq, p % nq]).astype(np.float64) * (L / nq) + L / (2 * ng)
+    target = np.array([[37.3], [5.9], [101.7]])
+    d = f32(target - q)
+    sim = C.Simulation(config(nq, ng, L))
+    sim.init_tables()
+    sim.d.copy_(dev(d))
+    got = host(sim.density())
+    ref = pm.density_contrast(d, nq, ng, L)
+    m3 = (ng / nq) ** 3
+    hot = ref > 0
+    assert hot.sum() == 8
+    # FP32 positions round the CIC fractions at ~1e-5 of a cell for every particle alike
+    np.testing.assert_allclose(got[hot], ref[hot], rtol=1e-4)
+    np.testing.assert_array_equal(got[~hot], -1.0)
+    assert (got + 1).sum() == pytest.approx(nq**3 * m3, rel=1e-6)
+
+
 # ---------------------------------------------------------------- force ----
 def _oracle_state(seed, nq, L, plin, growth, a=0.05):
     D1, _, D2, _ = growth(np.array([a]))
@@ -250,7 +272,8 @@ def test_single_cola_step_vs_oracle(plin, growth):
         assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
 
 
-def test_step_host_matches_device_step(plin, growth):
+@pytest.mark.parametrize("node", [11, 39])
+def test_step_host_matches_device_step(node, plin, growth):
     # the host-buffer entry point copies in, runs the same node and copies back
     nq, ng, L = 32, 96, 128.0
     ref = _oracle_state(9, nq, L, plin, growth, a=0.3)
@@ -259,11 +282,11 @@ def test_step_host_matches_device_step(plin, growth):
     sim = C.Simulation(config(nq, ng, L))
     sim.init_tables()
     sim.load_state(*(dev(st[k]) for k in ("d", "v", "psi1", "psi2")))
-    sim.step(11)
+    sim.step(node)
     want_d, want_v = host(sim.d), host(sim.v)
     hst = [torch.as_tensor(st[k], dtype=torch.float32).pin_memory() for k in ("d", "v", "psi1", "psi2")]
     sim.load_state(*(torch.zeros_like(x, device="cuda") for x in hst))  # the call must bring the state in
-    sim.step_host(C.make_state(*hst), 11)
+    sim.step_host(C.make_state(*hst), node)
     np.testing.assert_array_equal(hst[0].numpy(), want_d)
     np.testing.assert_array_equal(hst[1].numpy(), want_v)
     np.testing.assert_array_equal(hst[2].numpy(), st["psi1"])  # inputs only
