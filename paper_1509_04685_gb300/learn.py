@@ -198,6 +198,24 @@ def pk_deviation(k, p, p_ref, kmax: float = 1.0):
     return float(np.mean(np.abs(p[sel] / p_ref[sel] - 1.0)))
 
 
+def golden_section(f, lo: float, hi: float, iters: int = 8):
+    """Minimum of a unimodal f on [lo, hi] by golden-section search: iters + 2
+    evaluations, the bracket shrinking by 0.618 per iteration.  Returns (x, f(x))."""
+    r = (np.sqrt(5.0) - 1.0) / 2.0
+    x1, x2 = hi - r * (hi - lo), lo + r * (hi - lo)
+    f1, f2 = f(x1), f(x2)
+    for _ in range(iters):
+        if f1 < f2:
+            hi, x2, f2 = x2, x1, f1
+            x1 = hi - r * (hi - lo)
+            f1 = f(x1)
+        else:
+            lo, x1, f1 = x1, x2, f2
+            x2 = lo + r * (hi - lo)
+            f2 = f(x2)
+    return (x1, f1) if f1 < f2 else (x2, f2)
+
+
 def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: float = 1.0, rounds: int = 2,
                      device="cuda", use_net: bool = True):
     """Fit the least-squares filter's outcome on the training seeds: with
@@ -236,25 +254,10 @@ def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: 
                 dev.append(pk_deviation(k, p.cpu().numpy(), p3, kmax))
         return float(np.mean(dev))
 
-    def golden(f, lo, hi, iters=8):
-        r = (np.sqrt(5.0) - 1.0) / 2.0
-        x1, x2 = hi - r * (hi - lo), lo + r * (hi - lo)
-        f1, f2 = f(x1), f(x2)
-        for _ in range(iters):
-            if f1 < f2:
-                hi, x2, f2 = x2, x1, f1
-                x1 = hi - r * (hi - lo)
-                f1 = f(x1)
-            else:
-                lo, x1, f1 = x1, x2, f2
-                x2 = lo + r * (hi - lo)
-                f2 = f(x2)
-        return (x1, f1) if f1 < f2 else (x2, f2)
-
     g, c = 1.0, 0.0
     for _ in range(rounds):
-        c, _ = golden(lambda x: objective(g, x), -0.3, 4.0)
-        g, _ = golden(lambda x: objective(x, c), 0.0, 3.0)
+        c, _ = golden_section(lambda x: objective(g, x), -0.3, 4.0)
+        g, _ = golden_section(lambda x: objective(x, c), 0.0, 3.0)
     apply(g, c)
     torch.cuda.synchronize()
     del sim
