@@ -161,3 +161,27 @@ def test_lpt_frame_coefficients_satisfy_equation_of_motion():
         t = cm.step_table(c, np.array([a, a + 0.01]), g)
         assert acc1 == pytest.approx(t.c1[0], rel=1e-6)
         assert acc2 == pytest.approx(t.c2[0], rel=1e-6)
+
+
+def test_eh_transfer_depends_on_k_only_through_its_shape_variable():
+    # without baryons the fit is a function of q = k Theta^2 / (Omega_m h) (k in h/Mpc):
+    # two cosmologies agree at k scaled by their Omega_m h, and a CMB temperature enters as Theta^2
+    from dataclasses import replace
+    k = np.geomspace(1e-3, 30.0, 40)
+    a = replace(LCDM, omega_b=0.0, omega_m=0.25, omega_l=0.75, h=0.7)
+    b = replace(LCDM, omega_b=0.0, omega_m=0.3, omega_l=0.7, h=0.6)
+    np.testing.assert_allclose(cm.transfer_eh_nowiggle(k, a),
+                               cm.transfer_eh_nowiggle(k * (0.3 * 0.6) / (0.25 * 0.7), b), rtol=1e-12)
+    hot = replace(a, t_cmb=2.7255 * 1.1)
+    np.testing.assert_allclose(cm.transfer_eh_nowiggle(k, hot), cm.transfer_eh_nowiggle(k * 1.1**2, a), rtol=1e-12)
+
+
+def test_eh_baryon_suppression_vanishes_on_large_scales():
+    # the baryons' shape suppression switches on at k ~ 1/s (s ~ 150 Mpc): far below it
+    # the fit equals the zero-baryon one with the same Omega_m h, far above it it is lower
+    from dataclasses import replace
+    nob = replace(LCDM, omega_b=0.0)
+    k = np.array([1e-3, 3e-3])
+    np.testing.assert_allclose(cm.transfer_eh_nowiggle(k, LCDM), cm.transfer_eh_nowiggle(k, nob), rtol=1e-5)
+    assert cm.transfer_eh_nowiggle(3e-3, LCDM) < 0.99  # the check above is not just T ~ 1
+    assert cm.transfer_eh_nowiggle(1.0, LCDM) < 0.9 * cm.transfer_eh_nowiggle(1.0, nob)
