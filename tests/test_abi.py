@@ -92,3 +92,30 @@ def test_fof_entry_points_validate_before_launching():
     assert L.cola_fof_halos(ctypes.byref(cfg), fake, 0, fake, fake, fake, fake, fsize, None) == -1
     assert L.cola_mass_function(ctypes.byref(cfg), fake, fake, 10, 12.0, 0.0, 5, fake, None) == -1
     assert C.cola_launch_count() == 0
+
+
+def test_package_refuses_to_import_without_the_cuda_library(tmp_path):
+    # no fallback: a copy of the package without its built library does not import
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_1509_04685_gb300")
+    dst = tmp_path / "paper_1509_04685_gb300"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1509_04685_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "COLA CUDA library not built" in r.stderr
+
+
+def test_package_sources_do_not_reach_the_oracle():
+    # the product path neither imports nor runs anything under oracle/
+    src = os.path.join(ROOT, "paper_1509_04685_gb300")
+    for dirpath, _, files in os.walk(src):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+                mods = "|".join(m[:-3] for m in os.listdir(os.path.join(ROOT, "oracle")) if m.endswith(".py"))
+                assert not re.search(rf"\boracle\.({mods})\b", text), f
+                assert "oracle/" not in text and "import_module(\"oracle" not in text, f
