@@ -119,3 +119,21 @@ def test_package_sources_do_not_reach_the_oracle():
                 mods = "|".join(m[:-3] for m in os.listdir(os.path.join(ROOT, "oracle")) if m.endswith(".py"))
                 assert not re.search(rf"\boracle\.({mods})\b", text), f
                 assert "oracle/" not in text and "import_module(\"oracle" not in text, f
+
+
+def test_binding_argument_counts_match_the_header():
+    # every declared entry point is bound with as many arguments as the header gives it
+    import paper_1509_04685_gb300 as C
+    text = open(os.path.join(ROOT, "include", "cola.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    decls = re.findall(r"^\s*(?:int|int32_t|uint64_t|const char\*|void)\s+(cola_\w+)\s*\(([^;]*?)\)\s*;", text, re.M)
+    assert len(decls) >= 30
+    checked = 0
+    for name, params in decls:
+        fn = getattr(C.LIB, name)
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        if fn.argtypes is not None:
+            assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+            checked += 1
+    assert checked >= 25
