@@ -579,13 +579,13 @@ def main():
 
     # the outputs' cost, timed apart from the step: P(k) and the redshift-space
     # multipoles of the current state on a 1024^3 estimator mesh (the paper's P(k)
-    # mesh), and the FoF halos (b = 0.2, >= 100 particles) with their catalogue
+    # mesh), and the FoF halos (b = 0.2, more than 100 particles) with their catalogue
     pk_ms = {}
     ng_pk = min(1024, w["ng"])
     fof_out = {}
 
     def run_fof():
-        fof_out["halos"] = int(sim.fof(0.2, 100)[1].numel())
+        fof_out["halos"] = int(sim.fof(0.2, 101)[1].numel())
 
     for name, call in (("power_spectrum", lambda: sim.power(ng_pk)), ("multipoles", lambda: sim.multipoles(ng_pk)),
                        ("power_spectrum_jing_iterated", lambda: sim.power(ng_pk, flags=C.PK_ALIAS_ITER)),

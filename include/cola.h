@@ -7,7 +7,7 @@
  * displacement is integrated in time with particle-mesh forces (Eq. 2), on the
  * time nodes of Eq. 3.  Sec. 2.2 describes the force as a PM solve on a mesh
  * PM_grid times finer than the particle grid with one forward and three
- * inverse FFTs per step; Sec. 2.4 the CIC power-spectrum estimator.
+ * inverse FFTs per step; Sec. 2.5 the CIC power-spectrum estimator.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -53,9 +53,9 @@ extern "C" {
 #define COLA_FLAG_PM_ONLY 1u /* App. B: plain PM, no LPT frame (v holds the full momentum) */
 #define COLA_FLAG_LEARNED 2u /* force = filtered coarse PM force + conv-net residual (cfg->net) */
 
-#define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.4) */
-#define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.4) */
-/* The full Jing (2005) correction, iterated (Sec. 2.4): divide each mode by
+#define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.5) */
+#define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.5) */
+/* The full Jing (2005) correction, iterated (Sec. 2.5): divide each mode by
  * C(m) = sum over images |n_i| <= 2 of W_CIC^2(m + ng n) (|m + ng n|/|m|)^n_eff,
  * n_eff per bin the log-slope of the previous estimate between neighbouring
  * bins (clamped to [-4, 4]); start from flags 1 | 2, three iterations.  Use
@@ -167,7 +167,7 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
 int cola_step_host(const cola_config* cfg, const cola_state* host, cola_state* dev, int32_t step, void* ws,
                    size_t ws_bytes, void* stream);
 
-/* Matter power spectrum (Sec. 2.4) of the state on a CIC mesh of side ng_pk
+/* Matter power spectrum (Sec. 2.5) of the state on a CIC mesh of side ng_pk
  * (2 <= ng_pk <= ng, even, 2^a 3^b 5^c).  `node` is the time node the
  * positions sit at; if a_out differs from a_node the positions are first
  * drifted to a_out on the fly with the state's momentum (no force
@@ -274,7 +274,7 @@ int cola_ensemble_launch(cola_ensemble* e, void* stream);
 void cola_ensemble_destroy(cola_ensemble* e);
 
 /* Friends-of-friends halos (Sec. 2.1: FoF, linking length 0.2 of the mean
- * inter-particle spacing; Sec. 2.4: halos of >= 100 particles with Warren
+ * inter-particle spacing; Sec. 2.5: halos of more than 100 particles with Warren
  * masses M = m_p N (1 - N^-0.6)).  Positions are q + d nq / L in units of the
  * mean spacing, periodic; two particles are friends when their minimum-image
  * separation is at most b (decided in FP32, each operation rounded once);
@@ -287,7 +287,8 @@ void cola_ensemble_destroy(cola_ensemble* e);
  * `stream` before returning, to report COLA_ENONFINITE (a non-finite position;
  * that particle is left alone) or COLA_ETIMEOUT (a bounded union-find retry
  * loop gave up).
- * cola_fof_halos: the groups of at least min_members particles, ordered by
+ * cola_fof_halos: the groups of at least min_members particles (the paper's
+ * samples: min_members = 101, "more than 100"), ordered by
  * root: halo_root[h], halo_size[h] (DEVICE int32 arrays with room for
  * nq^3 / min_members entries) and *n_halos (DEVICE int64).  Uses fws.
  * cola_mass_function: counts[i] (DEVICE int64[nbins]) = halos with

@@ -18,7 +18,7 @@ the paper and the textbook definitions it relies on:
 * ``pm``        -- CIC deposit, k-space Green's function + ik gradient, CIC
   gather: the particle-mesh force (Sec. 2.2, Eq. 2 right-hand side).
 * ``cola``      -- the COLA kick-drift-kick loop in the LPT frame (Eqs. 1-2).
-* ``power``     -- the matter P(k) estimator (Sec. 2.4).
+* ``power``     -- the matter P(k) estimator (Sec. 2.5).
 * ``fof``       -- friends-of-friends groups (linking length b of the mean
   spacing), halo catalogue with Warren masses, mass function (Secs. 2.1, 2.4).
 * ``dft``       -- a direct O(N^2) DFT used to pin numpy's FFT.

@@ -1,6 +1,6 @@
 """Friends-of-friends halo finder and halo mass function (Sec. 2.1: FoF of
-Davis et al. 1985, linking length b = 0.2; Sec. 2.4: halos of at least
-100 particles, masses with the Warren et al. 2006 correction
+Davis et al. 1985, linking length b = 0.2; Sec. 2.5: halos of more than
+100 particles, i.e. at least 101, masses with the Warren et al. 2006 correction
 M = m_p N (1 - N^-0.6)).
 
 Test infrastructure only (see ``oracle/__init__``).
@@ -113,7 +113,7 @@ def warren_mass(n, m_p: float):
     return m_p * n * (1.0 - n ** -0.6)
 
 
-def halo_catalog(group: np.ndarray, min_members: int = 100):
+def halo_catalog(group: np.ndarray, min_members: int = 101):
     """(root, size) of every group with at least min_members particles, by root."""
     roots, sizes = np.unique(group, return_counts=True)
     keep = sizes >= min_members

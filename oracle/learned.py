@@ -3,7 +3,8 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 The paper has no learned component; this is the correction the build adds on
-the PM_grid = 1 mesh (the paper warns PM_grid <= 1 is biased, Sec. 5).
+the PM_grid = 1 mesh (the paper finds coarser force meshes biased: PM_grid = 2
+against 3 moves the matter P(k) by about 1 % and the halo abundance more, Sec. 4.4).
 Definitions, shared by the CUDA path (which rounds weights and activations to
 BF16 and accumulates in FP32):
 

@@ -1,4 +1,4 @@
-"""Matter power spectrum estimator (Sec. 2.4: CIC assignment to a mesh, FFT,
+"""Matter power spectrum estimator (Sec. 2.5: CIC assignment to a mesh, FFT,
 band power P(k) = <|delta_k|^2> over the modes of a k-bin, CIC deconvolution,
 Jing 2005 aliasing correction).
 

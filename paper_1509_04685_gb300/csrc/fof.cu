@@ -1,5 +1,5 @@
 // Friends-of-friends halo finder (Sec. 2.1: FoF, linking length b = 0.2 mean
-// inter-particle spacings; Sec. 2.4: halos of at least 100
+// inter-particle spacings; Sec. 2.5: halos of more than 100
 // particles, Warren et al. 2006 masses M = m_p N (1 - N^-0.6)) and the halo
 // mass function.
 //

@@ -1,4 +1,4 @@
-// Matter power spectrum shells (Sec. 2.4): P(k) = <|delta_k|^2> over the modes
+// Matter power spectrum shells (Sec. 2.5): P(k) = <|delta_k|^2> over the modes
 // of each k-bin, with optional CIC deconvolution and the Jing (2005) CIC
 // aliasing correction, closed form or iterated.
 //

@@ -42,7 +42,7 @@ class Simulation:
         L.cola_step_host(self.cfg, host, self.state, j, self.ws, self.stream)
         self.node = min(j + 1, self.cfg.n_steps - 1)
 
-    def fof(self, b: float = 0.2, min_members: int = 100):
+    def fof(self, b: float = 0.2, min_members: int = 101):
         """Friends-of-friends groups of the current positions: (group label of
         every particle, halo roots, halo sizes) as device tensors, halos of at
         least min_members particles ordered by root."""

@@ -52,3 +52,24 @@ def test_linear_regime_power_grows_as_D1_squared():
     assert abs(r32[0] - 1) < 0.012
     assert abs(r32[1] - 1) < 0.04
     assert 3.0 < (1 - r16[0]) / (1 - r32[0]) < 5.5
+
+
+@pytest.mark.parametrize("j", [0, 17, 38])
+def test_snapshot_to_the_next_node_is_the_step_drift(j):
+    # A snapshot taken at a_out = a_{j+1} from node j's state after its kick
+    # (positions still at a_j) is exactly the drift that the step itself makes:
+    # same interval, same signs, same growth differences.
+    c = cm.Cosmology()
+    g = cm.Growth(c)
+    tab = cm.step_table(c, cm.time_nodes(0.05, 1.0, 40), g)
+    nq, ng, L = 8, 16, 32.0
+    rng = np.random.default_rng(5 + j)
+    st = {k: rng.standard_normal((3, nq**3)) * s for k, s in (("d", 0.4), ("v", 2.0), ("psi1", 1.0), ("psi2", 0.3))}
+    d0 = st["d"].copy()
+    cola.cola_step(st, j, tab, nq, ng, L)
+    kicked = dict(st, d=d0)
+    snap = cola.snapshot_displacement(kicked, tab.a[j], tab.a[j + 1], g, c, cm.drift_integral)
+    np.testing.assert_allclose(snap, st["d"], rtol=0, atol=1e-13 * np.abs(st["d"]).max())
+    # and a snapshot at the node itself moves nothing
+    same = cola.snapshot_displacement(kicked, tab.a[j], tab.a[j], g, c, cm.drift_integral)
+    np.testing.assert_array_equal(same, d0)

@@ -185,3 +185,15 @@ def test_eh_baryon_suppression_vanishes_on_large_scales():
     np.testing.assert_allclose(cm.transfer_eh_nowiggle(k, LCDM), cm.transfer_eh_nowiggle(k, nob), rtol=1e-5)
     assert cm.transfer_eh_nowiggle(3e-3, LCDM) < 0.99  # the check above is not just T ~ 1
     assert cm.transfer_eh_nowiggle(1.0, LCDM) < 0.9 * cm.transfer_eh_nowiggle(1.0, nob)
+
+
+def test_eh_transfer_matches_the_hand_worked_example():
+    # tests/golden/eh98_nowiggle_worked_example.txt: Eqs. 26 and 28-31 of
+    # Eisenstein & Hu (1998) worked one at a time for the Sec. 2.1 cosmology;
+    # a wrong digit in any of the fit's constants moves T0 at one of the three k
+    rows = [line.split()[1:] for line in open(os.path.join(HERE, "golden", "eh98_nowiggle_worked_example.txt"))
+            if line.startswith("k_T0")]
+    k = np.array([float(r[0]) for r in rows])
+    t0 = np.array([float(r[1]) for r in rows])
+    assert len(rows) == 3
+    np.testing.assert_allclose(cm.transfer_eh_nowiggle(k, LCDM), t0, rtol=2e-8)

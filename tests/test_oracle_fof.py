@@ -135,7 +135,7 @@ def _golden_masses():
 
 def test_particle_mass_and_warren_masses():
     g = _golden_masses()
-    # Sec. 2.1: the MICE-GC particle mass; Sec. 2.4: the mass of the smallest kept halos
+    # Sec. 2.1: the MICE-GC particle mass; Sec. 2.5: the mass of the smallest kept halos
     om, L, n, value, tol = g["particle_mass"]
     mp = fof.particle_mass(om, L, int(n))
     assert mp == pytest.approx(value, rel=tol)

@@ -156,3 +156,40 @@ def test_single_particle_matches_ewald_inverse_square():
     assert g_small == pytest.approx(1.0 / (4 * math.pi * r_small**2), rel=2e-3)
     # and by symmetry no force half a box away
     assert np.abs(_ewald_grad(np.array([[L / 2, 0.0, 0.0]]), L, alpha=5.0 / L)).max() < 1e-12
+
+
+def test_radial_filter_constant_and_hat_nodes():
+    # T = const is that constant everywhere (also past the last node); the hat
+    # on node b is 1 at k_b = b kmax / (nb - 1), 0 at the neighbouring nodes
+    # and 1/2 half-way: the node spacing and the interpolation
+    nb, kmax = 9, 4.0
+    k = np.linspace(0.0, 1.3 * kmax, 1001)
+    np.testing.assert_allclose(pm.radial_filter(k, np.full(nb, 0.625), kmax), 0.625, rtol=0, atol=1e-15)
+    dk = kmax / (nb - 1)
+    for b in (0, 3, nb - 1):
+        T = np.zeros(nb)
+        T[b] = 1.0
+        at = lambda kk: float(pm.radial_filter(np.array([kk]), T, kmax)[0])
+        assert at(b * dk) == pytest.approx(1.0, abs=1e-15)
+        for nbr in (b - 1, b + 1):
+            if 0 <= nbr < nb:
+                assert at(nbr * dk) == pytest.approx(0.0, abs=1e-15)
+                assert at(0.5 * (b + nbr) * dk) == pytest.approx(0.5, abs=1e-15)
+
+
+def test_filtered_force_mesh_node_spacing():
+    # inside force_mesh_from_delta the nodes sit at b sqrt(3) pi ng / (L (nb - 1)).
+    # A diagonal mode n = (m, m, m) has |k| = 2 pi sqrt(3) m / L, which is node b
+    # exactly when m = ng b / (2 (nb - 1)): ng = 16, nb = 9, b = 4 gives m = 4.
+    # The hat on node 4 passes that mode whole, the hats on nodes 3 and 5 not at
+    # all; a constant filter scales the force.
+    ng, L, eps, green = 16, 40.0, 0.2, 0.9
+    delta = single_mode_delta(ng, L, eps, (4, 4, 4))
+    F = pm.force_mesh_from_delta(delta, L, green)
+    tol = 1e-12 * np.abs(F).max()
+    np.testing.assert_allclose(pm.force_mesh_from_delta(delta, L, green, filt=np.full(5, 1.75)), 1.75 * F,
+                               rtol=0, atol=tol)
+    for b, expect in ((4, 1.0), (3, 0.0), (5, 0.0)):
+        T = np.zeros(9)
+        T[b] = 1.0
+        np.testing.assert_allclose(pm.force_mesh_from_delta(delta, L, green, filt=T), expect * F, rtol=0, atol=tol)

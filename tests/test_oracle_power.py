@@ -168,3 +168,40 @@ def test_local_slopes_of_a_power_law():
     s = power.local_slopes(k, 3.0 * k**-9.0)
     assert np.all(s == -power.NEFF_CLAMP)
     assert power.local_slopes(k[:1], k[:1])[0] == 0.0
+
+
+def test_cic_deconvolution_of_one_particle_averaged_over_the_cell():
+    # One particle at u0 + s, s uniform over the cell [u0, u0 + 1)^3 (u0 on a
+    # mesh node): its CIC density has <|rho_k|^2> = sum_n W^2(m + ng n), the
+    # cross terms between images averaging out, W = prod sinc^2(pi x / ng) the
+    # CIC window.  The deconvolved estimator must give that image sum divided by
+    # W^2(m), the raw one the sum itself.  Inside the cell each axis's factor of
+    # |rho_k|^2 is a quadratic polynomial in that axis's offset, so two
+    # Gauss-Legendre points per axis give the average exactly; what remains is
+    # the image sum's truncation at |n_i| <= 8 (below 1e-4 relative).
+    from oracle.pm import cic_deposit
+    ng, L, J = 8, 3.0, 8
+    x, wq = np.polynomial.legendre.leggauss(2)
+    x, wq = 0.5 * (x + 1.0), 0.5 * wq
+    u0 = np.array([2.0, 5.0, 0.0])
+    raw = np.zeros(ng // 2)
+    dec = np.zeros(ng // 2)
+    for (i, a), (j, b), (l, c) in itertools.product(enumerate(x), repeat=3):
+        w = wq[i] * wq[j] * wq[l]
+        delta = cic_deposit((u0 + np.array([a, b, c]))[:, None], ng) * ng**3 - 1.0
+        raw += w * power.power_from_delta(delta, L)[1]
+        dec += w * power.power_from_delta(delta, L, flags=power.DECONV_CIC)[1]
+    nx, ny, nz = power._modes(ng)
+    n2 = nx**2 + ny**2 + nz**2
+    c0 = power.jing_alias_sum(nx, ny, nz, ng, 0.0, images=J)
+    W2 = (np.sinc(nx / ng) * np.sinc(ny / ng) * np.sinc(nz / ng)) ** 4
+    wt = np.where((nz == 0) | (nz == ng // 2), 1.0, 2.0) * np.ones(n2.shape)
+    ib = np.floor(np.sqrt(n2) + 0.5).astype(int)
+    sel = (n2 > 0) & (ib <= ng // 2)
+    nm = np.bincount(ib[sel] - 1, weights=wt[sel], minlength=ng // 2)
+    exp_raw = L**3 * np.bincount(ib[sel] - 1, weights=(wt * c0)[sel], minlength=ng // 2) / nm
+    exp_dec = L**3 * np.bincount(ib[sel] - 1, weights=(wt * c0 / W2)[sel], minlength=ng // 2) / nm
+    np.testing.assert_allclose(raw, exp_raw, rtol=2e-4)
+    np.testing.assert_allclose(dec, exp_dec, rtol=2e-4)
+    # the window matters: at the largest bins W^2 is far from 1
+    assert dec[-1] / raw[-1] > 3.0
