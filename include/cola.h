@@ -250,12 +250,17 @@ int cola_filter_solve(const double* ATA, const double* ATy, int32_t nb, double r
  * an integration convenience.  Same output as cola_density (delta as float[ng^3],
  * deterministic).  The fixed-point deposit mesh lives in one file-scope device
  * array of 128^3 cells (16 MiB per GPU that loads the library, held until the
- * process exits): ng > 128 returns COLA_EUNSUPPORTED_SIZE.  Nothing is
- * allocated.  The first call on each device looks up the array's device
- * address (with that device current); make that first call before any stream
- * capture.  Every call shares the array, so calls that overlap on the GPU
- * (different streams or devices' contexts sharing it) race; each call clears
- * it first.  Non-finite particle data turns the whole output into NaN. */
+ * process exits): ng > 128 returns COLA_EUNSUPPORTED_SIZE, and so do the
+ * sizes cola_density rejects.  Nothing is allocated.  Outside stream capture
+ * every call looks up the array's device address on the current device (so a
+ * device reset needs nothing special); a call on a stream being captured
+ * uses the address found by the last uncaptured call on that device, so make
+ * one uncaptured call on each device first, and again after a device reset
+ * (otherwise the captured call returns COLA_EINVAL).  There is one array per
+ * device: calls that overlap in time on the same device (different streams
+ * or host threads) share it and race; calls on different devices do not.
+ * Each call clears the cells it uses first.  Non-finite particle data turns
+ * the whole output into NaN; the next clean call is unaffected. */
 int cola_density_noalloc(const cola_config* cfg, const cola_state* st, float* delta, void* stream);
 
 /* Ensembles of independent realisations (Sec. 6 uses 48 realisations to beat

@@ -29,8 +29,9 @@ import numpy as np
 
 from .philox import white_noise_grid
 
-# FFT backend: numpy.fft (pocketfft), or scipy.fft's pocketfft with worker
-# threads when FFT_WORKERS > 1 (same algorithm; used for full-size references)
+# FFT backend of the 2LPT and PM transforms: numpy.fft (pocketfft), or
+# scipy.fft's pocketfft with worker threads when FFT_WORKERS > 1 (same
+# algorithm; used for full-size references and the timed CPU baseline)
 FFT_WORKERS = 1
 
 

@@ -32,7 +32,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .lpt import kgrid
+from .lpt import _irfftn, _rfftn, kgrid
 
 
 def lagrangian_index(nq: int):
@@ -107,7 +107,7 @@ def force_mesh_from_delta(delta: np.ndarray, L: float, green: float, filt=None) 
     kx, ky, kz, nx, ny, nz = kgrid(ng, L)
     k2 = kx**2 + ky**2 + kz**2
     k2[0, 0, 0] = 1.0
-    dk = np.fft.rfftn(delta)
+    dk = _rfftn(delta)
     phik = -green * dk / k2
     if filt is not None:
         phik = phik * radial_filter(np.sqrt(k2), np.asarray(filt, dtype=np.float64), np.sqrt(3.0) * np.pi * ng / L)
@@ -115,7 +115,7 @@ def force_mesh_from_delta(delta: np.ndarray, L: float, green: float, filt=None) 
     out = []
     for kj, nyq in ((kx, nx), (ky, ny), (kz, nz)):
         kd = np.where(nyq, 0.0, kj)
-        out.append(np.fft.irfftn(-1j * kd * phik, s=delta.shape, axes=(0, 1, 2)))
+        out.append(_irfftn(-1j * kd * phik, delta.shape))
     return np.stack(out)
 
 

@@ -8,15 +8,6 @@
 
 namespace cola {
 
-static bool factorable(int n) {
-    if (n < 1) return false;
-    for (int p : {2, 3, 5})
-        while (n % p == 0) n /= p;
-    return n == 1;
-}
-
-static bool mesh_ok(int n) { return n >= 4 && n % 2 == 0 && n <= kMaxFft && factorable(n) && factorable(n / 2); }
-
 static int check_config(const cola_config* c) {
     if (!c) return COLA_EINVAL;
     if (!mesh_ok(c->nq) || !mesh_ok(c->ng)) return COLA_EUNSUPPORTED_SIZE;

@@ -192,6 +192,18 @@ struct SmallDft<12> {
 // FFT plan: n = product of radices (applied in order), n <= kMaxFft
 // ---------------------------------------------------------------------------
 constexpr int kMaxFft = 4096;   // largest line length
+
+// n has no prime factor other than 2, 3 and 5
+inline bool factorable(int n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+// a mesh or lattice side every transform of the library can run: even, at
+// least 4, at most kMaxFft, and n and n/2 factorable (the real transforms run
+// n/2-point complex ones)
+inline bool mesh_ok(int n) { return n >= 4 && n % 2 == 0 && n <= kMaxFft && factorable(n) && factorable(n / 2); }
 constexpr int kMaxRadices = 16;
 
 // Exact division by a runtime constant d for numerators n with n * d < 2^32:

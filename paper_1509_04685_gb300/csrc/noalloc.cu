@@ -24,17 +24,26 @@ constexpr int kMaxDevices = 64;
 static unsigned long long* g_scratch_ptr[kMaxDevices];
 static std::mutex g_scratch_mutex;
 
-// Device address of the array on the current device, looked up once per
-// device.  The symbol name is only a host-side stand-in: it must not be handed
-// to a kernel; cudaGetSymbolAddress gives the real device address.
-static int scratch_for_current_device(unsigned long long** out) {
+// Device address of the array on the current device.  The symbol name is only
+// a host-side stand-in: it must not be handed to a kernel; cudaGetSymbolAddress
+// gives the real device address.  Outside stream capture the address is looked
+// up on every call, so a device reset (after which the module is loaded again
+// and the array may move) never leaves a stale address behind.  While `s` is
+// being captured the lookup is not made (it is not a capturable call): the
+// address cached by the last uncaptured call on this device is used, and with
+// none cached the call fails with COLA_EINVAL.
+static int scratch_for_current_device(cudaStream_t s, unsigned long long** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return COLA_ECUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return COLA_ECUDA;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return COLA_ECUDA;
         g_scratch_ptr[dev] = static_cast<unsigned long long*>(p);
+    } else if (!g_scratch_ptr[dev]) {
+        return COLA_EINVAL;
     }
     *out = g_scratch_ptr[dev];
     return COLA_OK;
@@ -55,15 +64,20 @@ using namespace cola;
 
 extern "C" int cola_density_noalloc(const cola_config* cfg, const cola_state* st, float* delta, void* stream) {
     if (!cfg || !st || !st->d || !delta) return COLA_EINVAL;
-    if (cfg->ng < 4 || cfg->ng % 2 || cfg->nq < 4 || cfg->nq % 2 || !(cfg->box > 0.0)) return COLA_EINVAL;
-    if (cfg->ng > kNoAllocMaxNg) return COLA_EUNSUPPORTED_SIZE;  // scratch holds at most 128^3 cells
-    unsigned long long* scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
-    if (rc) return rc;
+    if (!(cfg->box > 0.0)) return COLA_EINVAL;
+    // the sizes cola_density accepts, and no more cells than the array holds
+    if (!mesh_ok(cfg->nq) || !mesh_ok(cfg->ng) || cfg->ng > kNoAllocMaxNg) return COLA_EUNSUPPORTED_SIZE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long* scratch = nullptr;
+    int rc = scratch_for_current_device(s, &scratch);
+    if (rc) return rc;
     const size_t n3 = (size_t)cfg->ng * cfg->ng * cfg->ng;
     int* status = reinterpret_cast<int*>(scratch + kNoAllocCells);
-    // the array keeps whatever the last call left: start from zero counts and a clear flag
+    // The fix-up kernel clears every count it reads, and device arrays start at
+    // zero, so after a completed call the counts are already zero.  The clear
+    // guards against a previous call that stopped between its deposit and its
+    // fix-up (a failed launch) and leaves the array dirty; it costs about as
+    // much as one read of n3 counts.  The poison flag is cleared the same way.
     if (cudaMemsetAsync(scratch, 0, n3 * sizeof(unsigned long long), s) != cudaSuccess) return COLA_ECUDA;
     if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return COLA_ECUDA;
     if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, scratch, cfg->nq, cfg->ng, cfg->box, nullptr, status,
