@@ -167,6 +167,28 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
 int cola_step_host(const cola_config* cfg, const cola_state* host, cola_state* dev, int32_t step, void* ws,
                    size_t ws_bytes, void* stream);
 
+/* Checkpoint and resume of a run (the paper has no counterpart: its runs
+ * restart from the initial-condition seed).  A checkpoint is one HOST buffer
+ * of cola_checkpoint_bytes: a 256-byte header (magic "COLACKP1", format
+ * version, every field of cfg except the net pointer, the next time node to
+ * run, the array size) followed by d, v, psi1, psi2 (each 3 Nq^3 float32, SoA,
+ * as on the device).  The workspace is not part of it: cola_init rebuilds the
+ * tables and twiddles bit for bit and the deposit mesh is all-zero between
+ * calls, so after cola_init on a fresh workspace and cola_checkpoint_load,
+ * cola_step(node), cola_step(node + 1), ... continue the run bit-identically.
+ * cola_checkpoint_save copies st (DEVICE) into `host` and returns once the
+ * copies have landed; node in [0, n_steps).  cola_checkpoint_load checks that
+ * the header is this configuration's, field for field (COLA_EINVAL if not, or
+ * if host_bytes is short, before any copy), copies the arrays into st and
+ * returns the stored node in *node (HOST int32) once they have landed.  The
+ * buffer is read back on a host of the same byte order.  COLA_ECUDA on a
+ * failed copy. */
+int cola_checkpoint_bytes(const cola_config* cfg, size_t* bytes);
+int cola_checkpoint_save(const cola_config* cfg, const cola_state* st, int32_t node, void* host, size_t host_bytes,
+                         void* stream);
+int cola_checkpoint_load(const cola_config* cfg, const void* host, size_t host_bytes, cola_state* st, int32_t* node,
+                         void* stream);
+
 /* Matter power spectrum (Sec. 2.5) of the state on a CIC mesh of side ng_pk
  * (2 <= ng_pk <= ng, even, 2^a 3^b 5^c).  `node` is the time node the
  * positions sit at; if a_out differs from a_node the positions are first
@@ -303,6 +325,14 @@ void cola_ensemble_destroy(cola_ensemble* e);
 int cola_fof_workspace_size(const cola_config* cfg, size_t* bytes);
 int cola_fof(const cola_config* cfg, const cola_state* st, double b, int32_t* group, void* fws, size_t fws_bytes,
              void* stream);
+/* Bound on the retries of each union-find find, union and flattening loop of
+ * cola_fof (default 2^20, far above any real chain: 0 restores it; 1 <= cap
+ * <= 2^30).  A loop that reaches it stops and cola_fof returns COLA_ETIMEOUT
+ * (the labels are then not valid).  A hook for testing that error path
+ * without any wait running long; process-wide, not thread-safe against
+ * concurrent cola_fof calls. */
+int cola_fof_set_retry_cap(int32_t cap);
+
 int cola_fof_halos(const cola_config* cfg, const int32_t* group, int32_t min_members, int32_t* halo_root,
                    int32_t* halo_size, int64_t* n_halos, void* fws, size_t fws_bytes, void* stream);
 int cola_mass_function(const cola_config* cfg, const int32_t* halo_size, const int64_t* n_halos, int64_t max_halos,

@@ -26,7 +26,8 @@ Pins (tests/test_oracle_pm.py): sum of the CIC mesh = particle count; a
 particle on a node fills one cell; the net force on all particles vanishes;
 a prescribed single Fourier mode gives the closed-form force; a single
 particle's force matches the periodic point-mass (Ewald) force beyond a few
-cells; direct DFT vs numpy FFT.
+cells; direct DFT vs numpy FFT; lattice_wave_force equals pm_force on whole
+meshes with m = 1 .. 4 cells per spacing along each axis.
 """
 from __future__ import annotations
 
@@ -125,3 +126,67 @@ def pm_force(d, nq: int, ng: int, L: float, green: float):
     delta = cic_deposit(u, ng) * (ng / nq) ** 3 - 1.0
     fm = force_mesh_from_delta(delta, L, green)
     return np.stack([cic_gather(fm[j], u) for j in range(3)])
+
+
+def lattice_wave_force(dline, nq: int, ng: int, L: float, green: float, axis: int = 0) -> np.ndarray:
+    """The force (3, Np) that pm_force gives for the Lagrangian lattice displaced
+    along one axis only, by an amount that depends only on the lattice index
+    along that axis: d_axis(p) = dline[i_axis(p)], the other components zero.
+
+    Same readings as pm_force, computed exactly on a smaller periodic cell: with
+    m = ng / nq an integer, the lattice repeats every m cells across the axis,
+    so the density, the potential and the force repeat too, and only the modes
+    whose transverse indices are multiples of nq are present.  Those are the
+    modes of an ng x m x m mesh whose cells keep the size L / ng (transverse
+    wavenumbers 2 pi n / (m L / ng)); a transverse index n = +-m/2 there is the
+    full mesh's Nyquist plane.  Every particle of one line sits at the same
+    place in that cell (transverse mesh coordinate 1/2), so one line of nq
+    particles gives everyone's force."""
+    if ng % nq:
+        raise ValueError("needs ng a multiple of nq")
+    m = ng // nq
+    dline = np.asarray(dline, dtype=np.float64)
+    u = np.mod(np.arange(nq) * m + 0.5 + dline * (ng / L), ng)
+    shape = (ng, m, m)
+    c0 = np.floor(u).astype(np.int64)
+    f = u - c0
+    rho = np.zeros(shape)
+    for dx in (0, 1):
+        wx = f if dx else 1.0 - f
+        ix = (c0 + dx) % ng
+        for iy in (0, 1 % m):
+            for iz in (0, 1 % m):
+                np.add.at(rho, (ix, iy, iz), 0.25 * wx)
+    delta = rho * (ng / nq) ** 3 - 1.0
+    dk = np.fft.rfftn(delta)
+    nx = np.fft.fftfreq(ng, d=1.0 / ng)[:, None, None]
+    nt = np.fft.fftfreq(m, d=1.0 / m)[None, :, None]
+    nh = np.arange(m // 2 + 1, dtype=np.float64)[None, None, :]
+    cell = L / ng
+    kx = 2.0 * np.pi * nx / L
+    ky = 2.0 * np.pi * nt / (m * cell)
+    kz = 2.0 * np.pi * nh / (m * cell)
+    k2 = kx**2 + ky**2 + kz**2
+    k2[0, 0, 0] = 1.0
+    phik = -green * dk / k2
+    phik[0, 0, 0] = 0.0
+    even = m % 2 == 0
+    kdx = np.where(np.abs(nx) == ng // 2, 0.0, kx)
+    kdy = np.where(even & (np.abs(nt) == m // 2), 0.0, ky)
+    kdz = np.where(even & (nh == m // 2), 0.0, kz)
+    line = np.zeros((3, nq))
+    for j, kd in enumerate((kdx, kdy, kdz)):
+        fm = np.fft.irfftn(-1j * kd * phik, s=shape, axes=(0, 1, 2))
+        # gather: weights 1/2 to transverse cells 0 and 1 on both transverse axes
+        for dx in (0, 1):
+            wx = f if dx else 1.0 - f
+            ix = (c0 + dx) % ng
+            for iy in (0, 1 % m):
+                for iz in (0, 1 % m):
+                    line[j] += 0.25 * wx * fm[ix, iy, iz]
+    # the axis-0 cell's components (along, across, across) -> the lattice's axes
+    comp = [1, 2]
+    comp.insert(axis, 0)
+    idx = np.arange(nq)
+    lat = np.meshgrid(idx, idx, idx, indexing="ij")[axis].reshape(-1)
+    return np.stack([line[comp[c]][lat] for c in range(3)])

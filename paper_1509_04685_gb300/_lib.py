@@ -101,6 +101,10 @@ def _load():
         "cola_profile_stop": ([vp, vp, i32], ctypes.c_int),
         "cola_num_kernel_ids": ([], i32),
         "cola_kernel_name": ([i32], ctypes.c_char_p),
+        "cola_fof_set_retry_cap": ([i32], ctypes.c_int),
+        "cola_checkpoint_bytes": ([cfgp, ctypes.POINTER(sz)], ctypes.c_int),
+        "cola_checkpoint_save": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
+        "cola_checkpoint_load": ([cfgp, vp, sz, stp, ctypes.POINTER(i32), vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -263,6 +267,10 @@ def cola_step_host(cfg, host: cola_state, dev: cola_state, step: int, ws, stream
                               ws.numel() * ws.element_size(), _stream(stream)), "cola_step_host")
 
 
+def cola_fof_set_retry_cap(cap: int):
+    _check(LIB.cola_fof_set_retry_cap(cap), "cola_fof_set_retry_cap")
+
+
 def cola_fof_workspace_size(cfg) -> int:
     out = ctypes.c_size_t(0)
     _check(LIB.cola_fof_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "cola_fof_workspace_size")
@@ -298,6 +306,25 @@ def cola_power_multipoles(cfg, st: cola_state, node: int, a_out: float, ng_pk: i
     _check(LIB.cola_power_multipoles(ctypes.byref(cfg), ctypes.byref(st), node, a_out, ng_pk, flags, _ptr(k),
                                      _ptr(p0), _ptr(p2), _ptr(p4), _ptr(nmodes), k.numel(), _ptr(ws),
                                      ws.numel() * ws.element_size(), _stream(stream)), "cola_power_multipoles")
+
+
+def cola_checkpoint_bytes(cfg) -> int:
+    out = ctypes.c_size_t(0)
+    _check(LIB.cola_checkpoint_bytes(ctypes.byref(cfg), ctypes.byref(out)), "cola_checkpoint_bytes")
+    return out.value
+
+
+def cola_checkpoint_save(cfg, st: cola_state, node: int, host, stream=None):
+    """host: a HOST uint8 tensor (pinned for DMA) of cola_checkpoint_bytes."""
+    _check(LIB.cola_checkpoint_save(ctypes.byref(cfg), ctypes.byref(st), node, _ptr(host),
+                                    host.numel() * host.element_size(), _stream(stream)), "cola_checkpoint_save")
+
+
+def cola_checkpoint_load(cfg, host, st: cola_state, stream=None) -> int:
+    node = ctypes.c_int32(-1)
+    _check(LIB.cola_checkpoint_load(ctypes.byref(cfg), _ptr(host), host.numel() * host.element_size(),
+                                    ctypes.byref(st), ctypes.byref(node), _stream(stream)), "cola_checkpoint_load")
+    return node.value
 
 
 def cola_density(cfg, st: cola_state, delta, ws, stream=None):

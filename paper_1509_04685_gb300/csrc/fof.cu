@@ -27,7 +27,8 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kUnionCap = 1 << 20;  // bound on the retries of one find or union
+constexpr int kUnionCap = 1 << 20;  // default bound on the retries of one find or union
+int g_union_cap = kUnionCap;        // the bound in use (cola_fof_set_retry_cap)
 constexpr double kRhoCrit = 2.77536627e11;  // 3 H0^2 / (8 pi G) in h^2 Msun Mpc^-3
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -221,8 +222,8 @@ int exclusive_scan(int* a, long long n, int* sums, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // union-find over particle indices; parent[x] <= x always holds
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int fof_find(int* parent, int x, int* status) {
-    for (int it = 0; it < kUnionCap; ++it) {
+__device__ __forceinline__ int fof_find(int* parent, int x, int* status, int cap) {
+    for (int it = 0; it < cap; ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) return x;
         const int gp = __ldcg(parent + px);
@@ -233,10 +234,10 @@ __device__ __forceinline__ int fof_find(int* parent, int x, int* status) {
     return x;
 }
 
-__device__ __forceinline__ void fof_unite(int* parent, int a, int b, int* status) {
-    for (int it = 0; it < kUnionCap; ++it) {
-        a = fof_find(parent, a, status);
-        b = fof_find(parent, b, status);
+__device__ __forceinline__ void fof_unite(int* parent, int a, int b, int* status, int cap) {
+    for (int it = 0; it < cap; ++it) {
+        a = fof_find(parent, a, status, cap);
+        b = fof_find(parent, b, status, cap);
         if (a == b) return;
         if (a > b) {
             const int t = a;
@@ -268,16 +269,16 @@ __global__ void k_fof_init(int* parent, long long np) {
 __device__ __forceinline__ int wrap_cell(int c, int nq) { return c < 0 ? c + nq : (c >= nq ? c - nq : c); }
 
 __device__ __forceinline__ void link_candidate(const float4& a, const float4& o, float nqf, float half, float b2,
-                                               int* parent, int* status) {
+                                               int* parent, int* status, int cap) {
     const float dx = min_image(__fsub_rn(a.x, o.x), nqf, half);
     const float dy = min_image(__fsub_rn(a.y, o.y), nqf, half);
     const float dz = min_image(__fsub_rn(a.z, o.z), nqf, half);
     const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (r2 <= b2) fof_unite(parent, __float_as_int(a.w), __float_as_int(o.w), status);
+    if (r2 <= b2) fof_unite(parent, __float_as_int(a.w), __float_as_int(o.w), status, cap);
 }
 
 __global__ void k_fof_link(const float4* __restrict__ sorted, const int* __restrict__ start, long long np, int nq,
-                           float b2, float reach, int* parent, int* status) {
+                           float b2, float reach, int* parent, int* status, int cap) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < np;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -310,7 +311,7 @@ __global__ void k_fof_link(const float4* __restrict__ sorted, const int* __restr
             const int j1 = start[cell + 1];
             for (int j = start[cell]; j < j1; ++j) {
                 const float4 q = sorted[j];
-                if (j > k) link_candidate(a, q, nqf, half, b2, parent, status);
+                if (j > k) link_candidate(a, q, nqf, half, b2, parent, status, cap);
             }
         }
         return;
@@ -324,18 +325,18 @@ __global__ void k_fof_link(const float4* __restrict__ sorted, const int* __restr
                 const int cell = (cx * nq + cy) * nq + wrap_cell(c[2] + oz, nq);
                 const int j1 = start[cell + 1];
                 for (int j = start[cell] > k + 1 ? start[cell] : (int)k + 1; j < j1; ++j)
-                    link_candidate(a, sorted[j], nqf, half, b2, parent, status);
+                    link_candidate(a, sorted[j], nqf, half, b2, parent, status, cap);
             }
         }
     }
 }
 
 // every label becomes its root, the smallest member of its group
-__global__ void k_fof_flatten(int* parent, long long np, int* status) {
+__global__ void k_fof_flatten(int* parent, long long np, int* status, int cap) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     int x = (int)p;
-    for (int it = 0; it < kUnionCap; ++it) {
+    for (int it = 0; it < cap; ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) {
             parent[p] = x;
@@ -406,6 +407,12 @@ int read_status(const int* dev_status, cudaStream_t s) {
 
 extern "C" {
 
+int cola_fof_set_retry_cap(int32_t cap) {
+    if (cap < 0 || cap > (1 << 30)) return COLA_EINVAL;
+    cola::g_union_cap = cap ? cap : cola::kUnionCap;
+    return COLA_OK;
+}
+
 int cola_fof_workspace_size(const cola_config* cfg, size_t* bytes) {
     long long np = 0;
     if (!bytes) return COLA_EINVAL;
@@ -441,8 +448,9 @@ int cola_fof(const cola_config* cfg, const cola_state* st, double b, int32_t* gr
     k_fof_scatter<<<nb, T, 0, s>>>(st->d, np, cfg->nq, inv, cursor, sorted);
     k_fof_init<<<nb, T, 0, s>>>(group, np);
     // cells wider than the linking length by a margin far above FP32 rounding
-    k_fof_link<<<nb, T, 0, s>>>(sorted, start, np, cfg->nq, (float)(b * b), (float)b + 0.01f, group, status);
-    k_fof_flatten<<<nb, T, 0, s>>>(group, np, status);
+    k_fof_link<<<nb, T, 0, s>>>(sorted, start, np, cfg->nq, (float)(b * b), (float)b + 0.01f, group, status,
+                                  g_union_cap);
+    k_fof_flatten<<<nb, T, 0, s>>>(group, np, status, g_union_cap);
     if (int rc = check_launch()) return rc;
     return read_status(status, s);
 }

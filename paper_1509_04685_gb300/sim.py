@@ -3,6 +3,7 @@ state (four SoA float32 tensors of shape (3, nq^3)) and the workspace, and
 forwards every call to the library.  No arithmetic of the method happens here."""
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -31,6 +32,27 @@ class Simulation:
     def load_state(self, d, v, psi1, psi2):
         for dst, src in ((self.d, d), (self.v, v), (self.psi1, psi1), (self.psi2, psi2)):
             dst.copy_(torch.as_tensor(src).reshape(3, -1))
+
+    def save_checkpoint(self, path: str):
+        """Write the run (config identity, next node, d, v, psi1, psi2) to a file
+        through cola_checkpoint_save."""
+        buf = torch.empty(L.cola_checkpoint_bytes(self.cfg), dtype=torch.uint8, pin_memory=True)
+        L.cola_checkpoint_save(self.cfg, self.state, self.node, buf, self.stream)
+        with open(path, "wb") as f:
+            f.write(buf.numpy().tobytes())
+
+    def load_checkpoint(self, path: str):
+        """Resume a run saved by save_checkpoint: rebuild the workspace tables
+        (cola_init), load the state and the next node."""
+        n = L.cola_checkpoint_bytes(self.cfg)
+        buf = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        with open(path, "rb") as f:
+            data = f.read()
+        if len(data) != n:
+            raise L.ColaError(-1, "load_checkpoint: file size")
+        buf.numpy()[:] = np.frombuffer(data, dtype=np.uint8)
+        self.init_tables()
+        self.node = L.cola_checkpoint_load(self.cfg, buf, self.state, self.stream)
 
     def step(self, j: int):
         L.cola_step(self.cfg, self.state, j, self.ws, self.stream)

@@ -137,3 +137,24 @@ def test_binding_argument_counts_match_the_header():
             assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
             checked += 1
     assert checked >= 25
+
+
+def test_checkpoint_size_and_header_checks_without_copying():
+    # the buffer size and every header check run before any copy
+    import numpy as np
+
+    import paper_1509_04685_gb300 as C
+    L = C.LIB
+    cfg = C.make_config(8, 24, 32.0, 0.05)
+    n = C.cola_checkpoint_bytes(cfg)
+    assert n == 256 + 4 * 3 * 8**3 * 4
+    fake = 1 << 40
+    st = C.cola_state(fake, fake, fake, fake)
+    buf = np.zeros(n, np.uint8)
+    node = ctypes.c_int32(-1)
+    p = buf.ctypes.data
+    assert L.cola_checkpoint_load(ctypes.byref(cfg), p, n, ctypes.byref(st), ctypes.byref(node), None) == -1  # no magic
+    assert L.cola_checkpoint_save(ctypes.byref(cfg), ctypes.byref(st), 40, p, n, None) == -1  # node out of range
+    assert L.cola_checkpoint_save(ctypes.byref(cfg), ctypes.byref(st), 3, p, n - 1, None) == -1  # short buffer
+    assert L.cola_checkpoint_load(ctypes.byref(cfg), p, n - 1, ctypes.byref(st), ctypes.byref(node), None) == -1
+    assert node.value == -1

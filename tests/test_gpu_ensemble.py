@@ -45,6 +45,31 @@ def test_graph_ensemble_matches_standalone_runs():
         np.testing.assert_array_equal(host(ref.d), f)
 
 
+def test_graph_ensemble_at_the_batched_workload_sizes():
+    # the batched workload's member sizes, 40 nodes, L = nq Mpc/h: one member
+    # each at 96^3 on 96^3, 128^3 on 256^3 and 160^3 on 480^3 (radices 2, 3, 5)
+    mem = [(C.make_config(nq, m * nq, float(nq), 0.05, 1.0, 40), seed)
+           for (nq, m), seed in zip([(96, 1), (128, 2), (160, 3)], (1, 17, 33))]
+    sims = [C.Simulation(cfg) for cfg, _ in mem]
+    ens = C.Ensemble([cfg for cfg, _ in mem], [s for _, s in mem], [sm.state for sm in sims], [sm.ws for sm in sims],
+                     nstreams=3)
+    ens.launch()
+    torch.cuda.synchronize()
+    got = [(host(sm.d).copy(), host(sm.v).copy()) for sm in sims]
+    for sm in sims:
+        assert sm.status() == 0
+    del ens, sims
+    torch.cuda.empty_cache()
+    for (cfg, seed), (d, v) in zip(mem, got):
+        ref = C.Simulation(cfg)
+        ref.ic(seed)
+        ref.run()
+        np.testing.assert_array_equal(host(ref.d), d)
+        np.testing.assert_array_equal(host(ref.v), v)
+        del ref
+        torch.cuda.empty_cache()
+
+
 def test_autotuned_tiles_keep_results():
     n = 96
     cfg = C.make_config(32, n, 128.0, 0.05, 1.0, 6)

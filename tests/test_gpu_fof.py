@@ -159,3 +159,27 @@ def test_fof_at_the_benchmarked_size():
         r2 = (dl[0] * dl[0] + dl[1] * dl[1]) + dl[2] * dl[2]
         friends = torch.nonzero(r2 <= b2).flatten()
         assert bool((g[friends] == g[sp]).all())
+
+
+def test_fof_retry_cap_reports_timeout_and_resets():
+    # every particle on one point: the union-find's chains are deepest there.
+    # With the retry bound at 1 the loops give up at once: COLA_ETIMEOUT, no hang;
+    # with the default bound restored the same call labels one group again.
+    nq, L = 16, 16.0
+    q = fof.lattice_sites(nq).astype(np.float64)
+    d = ((np.array([[3.3], [7.7], [0.1]]) - q) * (L / nq)).astype(np.float32)
+    s = _sim(nq, L)
+    s.d.copy_(dev(d))
+    g = torch.empty(nq**3, dtype=torch.int32, device="cuda")
+    fws = torch.empty(C.cola_fof_workspace_size(s.cfg), dtype=torch.uint8, device="cuda")
+    C.cola_fof_set_retry_cap(1)
+    try:
+        with pytest.raises(C.ColaError) as e:
+            C.cola_fof(s.cfg, s.state, 0.2, g, fws)
+        assert e.value.code == -5
+    finally:
+        C.cola_fof_set_retry_cap(0)
+    C.cola_fof(s.cfg, s.state, 0.2, g, fws)
+    assert bool((g == 0).all())
+    with pytest.raises(C.ColaError):
+        C.cola_fof_set_retry_cap(-1)

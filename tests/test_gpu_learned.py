@@ -1,7 +1,7 @@
 """Learned coarse-mesh correction: CUDA (BF16 tensor-core convolutions, FP32
 accumulation) against the FP64 oracle on the same BF16-rounded weights.
 Tolerances: filter-only force rel-L2 <= 1e-5 (FP32 path); net residual force
-and every gradient tensor rel-L2 <= 5e-2 and cosine >= 0.995 (BF16 weights and
+and every gradient tensor rel-L2 <= 2e-2 and cosine >= 0.999 (BF16 weights and
 activations, FP32 accumulation)."""
 import numpy as np
 import pytest
@@ -22,6 +22,7 @@ import paper_1509_04685_gb300 as C  # noqa: E402
 from gpu_util import dev, f32, host, rel_l2  # noqa: E402
 
 COSMO = cm.Cosmology()
+GRAD_REL, GRAD_COS = 2e-2, 0.999
 
 
 def _cos(a, b):
@@ -96,8 +97,9 @@ def test_filtered_force_and_net_residual_vs_oracle():
     f1 = host(sim.force(a))
     out, _ = ol.net_forward(x, pr)
     ref_res = np.stack([pm.cic_gather(green * out[j], u) for j in range(3)])
-    assert rel_l2(f1 - f0, ref_res) < 5e-2
-    assert _cos(f1 - f0, ref_res) > 0.995
+    e, c = rel_l2(f1 - f0, ref_res), _cos(f1 - f0, ref_res)
+    print("net residual force rel-L2, cosine:", e, c)
+    assert e < GRAD_REL and c > GRAD_COS, (e, c)
 
 
 def test_scale_factor_filter_rows_vs_oracle():
@@ -166,11 +168,14 @@ def test_net_gradients_vs_oracle():
     g = ol.net_backward(green * dmesh, cache, pr)
     assert host(loss)[0] == pytest.approx(lo, rel=2e-3)
     gh = host(grad)
+    errs = {}
     for k, (off, shape) in C.NET_OFFSETS.items():
         got = gh[off: off + int(np.prod(shape))]
         ref = g[k].reshape(-1)
-        assert rel_l2(got, ref) < 5e-2, k
-        assert _cos(got, ref) > 0.995, k
+        errs[k] = (rel_l2(got, ref), _cos(got, ref))
+    print("net gradient rel-L2, cosine per tensor:", errs)
+    for k, (e, c) in errs.items():
+        assert e < GRAD_REL and c > GRAD_COS, errs
 
 
 def test_filter_least_squares_recovers_a_known_filter():

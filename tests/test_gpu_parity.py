@@ -380,16 +380,29 @@ def test_redshift_space_multipoles_vs_oracle(pm_only, da, plin, growth):
 
 
 # ---------------------------------------------------------------- run ------
-def test_full_run_small_config_vs_oracle(plin, growth):
-    """32^3 particles on a 96^3 mesh, L = 128 Mpc/h, 40 linear steps z = 19 -> 0."""
+SAMPLINGS = {C.SAMPLING_LINEAR: "linear", C.SAMPLING_LOG: "log", C.SAMPLING_POW: "pow"}
+
+
+@pytest.mark.parametrize("sampling,p,a_init", [
+    (C.SAMPLING_LINEAR, 1.0, 0.05),      # the paper's optimal setup: 40 linear steps from z = 19
+    (C.SAMPLING_LOG, 1.0, 0.05),         # Sec. 4.2, Eq. 3 with f = ln a
+    (C.SAMPLING_POW, 0.5, 0.05),         # Sec. 4.2, f = a^p
+    (C.SAMPLING_POW, 0.8, 0.05),
+    (C.SAMPLING_LINEAR, 1.0, 0.1),       # Sec. 4.3: z_i = 9
+    (C.SAMPLING_LINEAR, 1.0, 1.0 / 40),  # z_i = 39
+    (C.SAMPLING_LINEAR, 1.0, 1.0 / 101), # z_i = 100
+])
+def test_full_run_small_config_vs_oracle(sampling, p, a_init, plin, growth):
+    """32^3 particles on a 96^3 mesh, L = 128 Mpc/h, 40 steps to z = 0 with the
+    paper's time samplings and initial redshifts."""
     nq, ng, L = 32, 96, 128.0
-    cfg = config(nq, ng, L)
+    cfg = config(nq, ng, L, a_init=a_init, sampling=sampling, sampling_p=p)
     sim = C.Simulation(cfg)
     sim.ic(seed=1)
     sim.run()
     assert sim.status() == 0
-    tab = cm.step_table(COSMO, cm.time_nodes(0.05, 1.0, 40), growth)
-    ref = _oracle_state(1, nq, L, plin, growth)
+    tab = cm.step_table(COSMO, cm.time_nodes(a_init, 1.0, 40, SAMPLINGS[sampling], p), growth)
+    ref = _oracle_state(1, nq, L, plin, growth, a=a_init)
     ocola.run(ref, tab, nq, ng, L)
     dq = L / nq
     rms = np.sqrt(np.mean(np.sum((host(sim.d) - ref["d"]) ** 2, axis=0)))

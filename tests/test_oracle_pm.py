@@ -193,3 +193,18 @@ def test_filtered_force_mesh_node_spacing():
         T = np.zeros(9)
         T[b] = 1.0
         np.testing.assert_allclose(pm.force_mesh_from_delta(delta, L, green, filt=T), expect * F, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_lattice_wave_force_equals_the_full_mesh_force(m, axis):
+    # the reduced periodic cell against brute force: pm_force on the whole mesh
+    nq, L, green = 8, 24.0, 0.8
+    ng = nq * m
+    dline = np.random.default_rng(10 * m + axis).standard_normal(nq) * 0.6 * L / nq
+    d = np.zeros((3, nq**3))
+    d[axis] = dline[pm.lagrangian_index(nq)[axis]]
+    full = pm.pm_force(d, nq, ng, L, green)
+    red = pm.lattice_wave_force(dline, nq, ng, L, green, axis)
+    assert np.abs(red - full).max() <= 1e-12 * np.abs(full).max()
+    assert np.abs(full[axis]).max() > 0.05
