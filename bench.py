@@ -44,6 +44,9 @@ WORKLOADS = {
     # the largest run's learned 1.5x form vs its plain 3x form, P(k) at z = 1, 0.5, 0
     "largest_learned": dict(name="cola_learned_768^3_particles_1152^3_vs_2304^3_mesh_L1536_40steps", nq=0, ng=0,
                             box=0.0),
+    # convergence in the number of time steps (10/20/40 against 80), every time sampling
+    # and both kick/drift forms, at 32^3/96^3 (L = 128) and 256^3/768^3 (L = 768)
+    "convergence": dict(name="cola_convergence_10-20-40_vs_80_steps_32^3_96^3_and_256^3_768^3", nq=0, ng=0, box=0.0),
 }
 
 
@@ -148,38 +151,41 @@ def run_ensemble(args, rank, world, C, torch, dist):
                        "parallelism": f"members sharded over {world} rank(s)"},
             "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
         }), flush=True)
-def run_learned(args, rank, world, C, torch, dist):
-    """The learned 1x-mesh form against the plain 3x-mesh form: 256^3
-    particles, L = 512 Mpc/h, 40 steps.  The correction is fitted on seeded
-    plain 3x runs (filter rows from every node of every run, the net on four
-    nodes of the first eight), then both forms run the held-out seeds.  The
-    value is the learned form's particle-steps/s; the line adds the plain 3x
-    form's, their ratio and the final P(k) deviation for k <= 1 h/Mpc."""
+def learned_study(C, torch, nq, box, train_seeds, test_seeds, net_iters, dev_index=0):
+    """The learned 1x-mesh form against the plain 3x-mesh form (config 4 at
+    nq = 256, L = 512 Mpc/h, 40 steps).  The radial filter is fitted by least
+    squares on every node of plain 3x runs of the training seeds and its
+    P(k) calibration on four of them; the learned form is the filtered 1x mesh
+    alone.  With net_iters > 0 the convolution net is also trained (on four
+    nodes of the first eight runs) and reported as a separate form.  Every form
+    then runs the held-out seeds; returns the timings and the final P(k)
+    deviation from the plain 3x form for k <= 1 h/Mpc."""
     import numpy as np
 
     from paper_1509_04685_gb300 import learn
 
-    nq, box = 256, 512.0
-    train_seeds = [1001 + 100 * rank + i for i in range(args.learned_train)]
-    test_seeds = [2001 + 100 * rank + i for i in range(args.learned_test)]
     t0 = time.perf_counter()
     corr = learn.LearnedCorrection(nfilter=16, seed=0, nfilter_a=8)
-    samples, final = learn.fit_filter_runs(corr, train_seeds, nq, box, keep_nodes=(10, 20, 30, 39))
-    samples = samples[: 4 * 8]
-    hist = learn.train(corr, samples, nq, box, iters=args.learned_iters, lr=3e-3,
-                       log_every=max(1, args.learned_iters // 4))
+    samples, final = learn.fit_filter_runs(corr, train_seeds, nq, box,
+                                           keep_nodes=(10, 20, 30, 39) if net_iters else ())
+    hist = []
+    if net_iters:
+        hist = learn.train(corr, samples[: 4 * 8], nq, box, iters=net_iters, lr=3e-3,
+                           log_every=max(1, net_iters // 4))
     del samples
     torch.cuda.empty_cache()
-    gain, boost = learn.calibrate_filter(corr, {s: final[s] for s in train_seeds[:4]}, nq, box)
+    cal = {s: final[s] for s in train_seeds[:4]}
+    gain, boost = learn.calibrate_filter(corr, cal, nq, box, use_net=False)
     t_train = time.perf_counter() - t0
-    cfg3 = C.make_config(nq, 3 * nq, box, A_INIT, 1.0, N_NODES)
-    cfg1 = C.make_config(nq, nq, box, A_INIT, 1.0, N_NODES)
-    cfgl = corr.config(nq, box)
-    sims = {"plain_3x": C.Simulation(cfg3), "plain_1x": C.Simulation(cfg1), "learned_1x": C.Simulation(cfgl)}
+    forms = {"plain_3x": C.make_config(nq, 3 * nq, box, A_INIT, 1.0, N_NODES),
+             "plain_1x": C.make_config(nq, nq, box, A_INIT, 1.0, N_NODES),
+             "learned_1x": corr.config(nq, box, use_net=False)}
+    if net_iters:
+        forms["learned_1x_net"] = corr.config(nq, box, use_net=True)
+    sims = {k: C.Simulation(cfg) for k, cfg in forms.items()}
     ms = {k: 0.0 for k in sims}
     pk = {k: [] for k in sims}
-    launches0 = C.cola_launch_count()
-    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks = Clocks(dev_index)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for key, sm in sims.items():  # one untimed run per form (kernel attributes, caches)
         sm.ic(test_seeds[0])
@@ -201,37 +207,113 @@ def run_learned(args, rank, world, C, torch, dist):
     k = k.cpu().numpy()
     sel = k <= 1.0
     ratio = {key: np.mean(np.stack(pk[key]), axis=0) / np.mean(np.stack(pk["plain_3x"]), axis=0) for key in pk}
-    dev = {key: float(np.max(np.abs(ratio[key][sel] - 1))) for key in ("plain_1x", "learned_1x")}
-    mdev = {key: float(np.mean(np.abs(ratio[key][(k > 0.1) & sel] - 1))) for key in ("plain_1x", "learned_1x")}
+    others = [key for key in sims if key != "plain_3x"]
+    dev = {key: float(np.max(np.abs(ratio[key][sel] - 1))) for key in others}
+    mdev = {key: float(np.mean(np.abs(ratio[key][(k > 0.1) & sel] - 1))) for key in others}
     nsteps = N_NODES * len(test_seeds)
-    ps = {key: nq**3 * nsteps / (ms[key] * 1e-3) for key in ms}
+    del sims
+    torch.cuda.empty_cache()
+    return {
+        "ms_per_step": {key: ms[key] / nsteps for key in ms},
+        "particle_steps_per_s": {key: nq**3 * nsteps / (ms[key] * 1e-3) for key in ms},
+        "speedup_vs_plain_3x": ms["plain_3x"] / ms["learned_1x"],
+        "pk_final": {"k_max": 1.0, "target_max_abs_dev": 0.01, "max_abs_dev": dev, "mean_abs_dev_0.1_to_1": mdev,
+                     "learned_within_target": dev["learned_1x"] <= 0.01,
+                     "ratio_learned": [round(float(x), 5) for x in ratio["learned_1x"][sel]],
+                     "ratio_plain_1x": [round(float(x), 5) for x in ratio["plain_1x"][sel]],
+                     "k": [round(float(x), 4) for x in k[sel]]},
+        "training": {"seconds": t_train, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
+                     "net_iters": net_iters, "net_loss": hist, "filter_gain": gain, "filter_boost": boost,
+                     "calibration_seeds": len(cal)},
+        "clocks": clk, "steps": nsteps,
+    }
+
+
+def run_learned(args, rank, world, C, torch, dist):
+    """Config 4: the learned 1x-mesh form (the filtered coarse mesh) against the
+    plain 3x-mesh form, 256^3 particles, L = 512 Mpc/h; the value is the learned
+    form's particle-steps/s (summed over replicas)."""
+    nq, box = 256, 512.0
+    train_seeds = [1001 + 100 * rank + i for i in range(args.learned_train)]
+    test_seeds = [2001 + 100 * rank + i for i in range(args.learned_test)]
+    launches0 = C.cola_launch_count()
+    st = learned_study(C, torch, nq, box, train_seeds, test_seeds, args.learned_iters,
+                       int(os.environ.get("LOCAL_RANK", "0")))
+    ps = st["particle_steps_per_s"]
     tot = torch.tensor([ps["learned_1x"], ps["plain_3x"]], device="cuda")
     if dist:
         dist.all_reduce(tot)
     if rank == 0:
         print(json.dumps({
             "metric": "particle-steps/s of the learned 1x-mesh form (256^3 particles, L=512 Mpc/h)",
-            "value": float(tot[0].item()), "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": N_NODES,
-            "ms_per_step": ms["learned_1x"] / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (bf16 convolutions)", "data": "synthetic",
+            "value": float(tot[0].item()), "unit": UNIT, "n_gpus": world, "steps": st["steps"], "warmup": N_NODES,
+            "ms_per_step": st["ms_per_step"]["learned_1x"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS["learned"]["name"], "nq": nq, "ng_learned": nq, "ng_plain": 3 * nq,
                        "box": box, "n_steps": N_NODES, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
-                       "filter": "16 radial nodes x 8 scale-factor rows, least squares on every node of the fine runs, "
-                                 "boost calibrated on 4 training seeds' final P(k)", "net_iters": args.learned_iters,
+                       "learned_form": "radial filter on the 1x mesh (16 nodes x 8 scale-factor rows, least squares "
+                                       "on every node of the fine runs, P(k)-calibrated boost); the convolution net "
+                                       "is reported apart as learned_1x_net when trained (--learned-iters)",
                        "parallelism": f"replicas{world}"},
-            "plain_3x": {"value": float(tot[1].item()), "ms_per_step": ms["plain_3x"] / nsteps},
-            "plain_1x": {"ms_per_step": ms["plain_1x"] / nsteps},
-            "speedup_vs_plain_3x": ps["learned_1x"] / ps["plain_3x"],
-            "pk_final": {"k_max": 1.0, "target_max_abs_dev": 0.01,
-                         "max_abs_dev": dev, "mean_abs_dev_0.1_to_1": mdev,
-                         "learned_within_target": dev["learned_1x"] <= 0.01,
-                         "ratio_learned": [round(float(x), 5) for x in ratio["learned_1x"][sel]],
-                         "ratio_plain_1x": [round(float(x), 5) for x in ratio["plain_1x"][sel]],
-                         "k": [round(float(x), 4) for x in k[sel]]},
-            "training": {"seconds": t_train, "loss": hist, "filter_gain": gain, "filter_boost": boost,
-                         "calibration_seeds": 4},
-            "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
+            "plain_3x": {"value": float(tot[1].item()), "ms_per_step": st["ms_per_step"]["plain_3x"]},
+            "forms": st["ms_per_step"], "speedup_vs_plain_3x": st["speedup_vs_plain_3x"],
+            "pk_final": st["pk_final"], "training": st["training"], "clocks": st["clocks"],
+            "gpu_launches": C.cola_launch_count() - launches0,
         }), flush=True)
+
+
+def run_convergence(args, rank, world, C, torch, dist):
+    """Convergence of the final P(k) in the number of time steps, in the spirit
+    of the paper's Sec. 4.1-4.3 study (there against MICE-GC, here internal):
+    runs of 10, 20 and 40 steps from z = 19, with the linear, log and a^0.5
+    samplings of Eq. 3 and with the standard or the Tassev et al. (2013) kick
+    and drift factors, against 80 linear steps with the standard factors from
+    the same seed.  Reported per run: max |P/P_80 - 1| for k <= 0.5 and k <= 1
+    h/Mpc (P(k) on the force mesh, final node), and the run's ms per step."""
+    import numpy as np
+
+    if rank != 0:
+        return
+    cases = [(32, 96, 128.0), (256, 768, 768.0)]
+    samplings = (("linear", C.SAMPLING_LINEAR, 1.0), ("log", C.SAMPLING_LOG, 1.0), ("a^0.5", C.SAMPLING_POW, 0.5))
+    out = {}
+    launches0 = C.cola_launch_count()
+    for nq, ng, box in cases:
+        def final_pk(n, sampling=C.SAMPLING_LINEAR, p=1.0, flags=0):
+            sim = C.Simulation(C.make_config(nq, ng, box, A_INIT, 1.0, n, sampling=sampling, sampling_p=p,
+                                             flags=flags))
+            sim.ic(seed=1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.run()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / n
+            if sim.status() != 0:
+                raise SystemExit(f"device status after the {n}-step run")
+            k, pk, _ = sim.power(ng, node=n - 1)
+            res = (k.cpu().numpy(), pk.cpu().numpy(), ms)
+            del sim
+            torch.cuda.empty_cache()
+            return res
+
+        k, p80, _ = final_pk(80)
+        rows = []
+        for kdk, flags in (("standard", 0), ("modified", C.FLAG_MODIFIED_KDK)):
+            for sname, samp, sp in samplings:
+                for n in (10, 20, 40):
+                    _, pn, ms = final_pk(n, samp, sp, flags)
+                    r = pn / p80 - 1
+                    rows.append({"steps": n, "sampling": sname, "kdk": kdk,
+                                 "max_dev_k<=0.5": float(np.max(np.abs(r[k <= 0.5]))),
+                                 "max_dev_k<=1": float(np.max(np.abs(r[k <= 1.0]))),
+                                 "ms_per_step": round(ms, 3)})
+        out[f"{nq}^3_{ng}^3_L{box:g}"] = {"k_nyquist": float(np.pi * ng / box), "runs": rows}
+    print(json.dumps({
+        "metric": "final P(k) deviation from 80 linear steps", "unit": "max |P/P_80 - 1|", "n_gpus": 1,
+        "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+        "config": {"workload": WORKLOADS["convergence"]["name"], "z_init": 1 / A_INIT - 1, "seed": 1},
+        "results": out, "gpu_launches": C.cola_launch_count() - launches0,
+    }), flush=True)
 
 
 def run_largest_learned(args, rank, world, C, torch, dist):
@@ -345,6 +427,17 @@ def algorithmic_bytes(name: str, nq: int, ng: int) -> float:
     M = ng**3 * 4.0                     # real mesh
     F = ng**3 * 8.0                     # fixed-point CIC mesh
     return {
+        # row bins: positions read, key + rank written (count); key, rank, positions and
+        # the bin offset read, index, CIC record and sorted position written (scatter);
+        # the ng^2 counts cleared, counted, scanned (read + write) and read
+        "bins": 68.0 * Np + 16.0 * ng * ng,
+        # each particle's CIC record and index read once, delta_k written
+        "dep_r2c": 20.0 * Np + Mc,
+        # three force components read, CIC records and indices read once, the
+        # 48-byte partial-sum records written
+        "c2r_gather": 3 * Mc + 20.0 * Np + 48.0 * Np,
+        # sorted position and partial-sum record, d, v, psi1, psi2 read; d, v written
+        "kick_drift": 52.0 * Np + 72.0 * Np,
         "deposit": 12.0 * Np + F,
         "fft_z_r2c_fix": 2 * F + Mc,
         "fft_y_fwd": 2 * Mc, "fft_x_fwd": 2 * Mc, "fft_x_inv": 2 * Mc,
@@ -367,8 +460,8 @@ def step_reference_bytes(nq: int, ng: int) -> float:
 
 # sources that define and launch the kernels of a step (profiles/ncu_traffic.json
 # holds counters taken on them; a change here makes the stored traffic stale)
-STEP_SOURCES = ("cola_common.cuh", "fft_static.cuh", "fft.cu", "fft_spec_large.cu", "fft_spec_small.cu", "pm.cu",
-                "api.cu")
+STEP_SOURCES = ("cola_common.cuh", "fft_static.cuh", "fft_fused.cuh", "particles.cuh", "fft.cu", "fft_spec_large.cu",
+                "fft_spec_small.cu", "pm.cu", "scan.cu", "api.cu")
 
 
 def csrc_digest() -> str:
@@ -528,7 +621,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-train", type=int, default=32, help="fine training runs (learned workload)")
     ap.add_argument("--learned-test", type=int, default=8, help="held-out seeds (learned workload)")
-    ap.add_argument("--learned-iters", type=int, default=300, help="Adam iterations of the net (learned workload)")
+    ap.add_argument("--learned-iters", type=int, default=0,
+                    help="Adam iterations of the convolution net (learned workload; 0: the filter alone)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-form summary of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -550,9 +645,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    if args.workload in ("ensemble", "learned", "largest_learned"):
-        {"ensemble": run_ensemble, "learned": run_learned,
-         "largest_learned": run_largest_learned}[args.workload](args, rank, world, C, torch, dist)
+    if args.workload in ("ensemble", "learned", "largest_learned", "convergence"):
+        {"ensemble": run_ensemble, "learned": run_learned, "largest_learned": run_largest_learned,
+         "convergence": run_convergence}[args.workload](args, rank, world, C, torch, dist)
         if dist:
             dist.destroy_process_group()
         return
@@ -648,6 +743,25 @@ def main():
     h2d = sum(x.numel() * x.element_size() for x in hst)
     d2h = sum(x.numel() * x.element_size() for x in hst[:2])
 
+    # config 4 alongside the headline: the learned 1x-mesh form against the plain
+    # 3x form (filter fitted on 8 training seeds, 4 held-out seeds), so that its
+    # speed and its P(k) deviation for k <= 1 h/Mpc are on the default line too
+    learned = None
+    if rank == 0 and args.workload == "full" and not args.no_learned:
+        del sim, hst, host_state
+        torch.cuda.empty_cache()
+        try:
+            st = learned_study(C, torch, 256, 512.0, [1001 + i for i in range(8)], [2001 + i for i in range(4)], 0,
+                               local)
+            learned = {"workload": WORKLOADS["learned"]["name"], "ms_per_step": st["ms_per_step"],
+                       "particle_steps_per_s": st["particle_steps_per_s"],
+                       "speedup_vs_plain_3x": st["speedup_vs_plain_3x"],
+                       "pk_final_max_abs_dev_k<=1": st["pk_final"]["max_abs_dev"],
+                       "pk_final_mean_abs_dev_0.1<k<=1": st["pk_final"]["mean_abs_dev_0.1_to_1"],
+                       "within_1pct": st["pk_final"]["learned_within_target"],
+                       "train_seeds": 8, "test_seeds": 4, "training_s": st["training"]["seconds"]}
+        except Exception as e:  # the headline stands without it
+            learned = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         line = {
@@ -672,6 +786,8 @@ def main():
                            "fof_after_nodes": args.warmup + args.steps},
             "cpu_baseline": cpu,
         }
+        if learned is not None:
+            line["learned_1x"] = learned
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -52,6 +52,14 @@ extern "C" {
 
 #define COLA_FLAG_PM_ONLY 1u /* App. B: plain PM, no LPT frame (v holds the full momentum) */
 #define COLA_FLAG_LEARNED 2u /* force = filtered coarse PM force + conv-net residual (cfg->net) */
+/* The modified kick and drift factors of Tassev, Zaldarriaga & Eisenstein (2013),
+ * the COLA paper Sec. 1 cites for Eq. 2, in place of the standard ones: the
+ * residual momentum is taken to vary as a^n, n = n_LPT = -2.5, about the time
+ * the force (kick: the node a_j) or the momentum (drift: the midpoint
+ * a_{j+1/2}) is known:  kick_j = (a_{j+1/2}^n - a_{j-1/2}^n) / (n a_j^n E(a_j)),
+ * drift_j = a_{j+1/2}^-n int_{a_j}^{a_{j+1}} a^n da / (a^3 E).  Snapshots between
+ * nodes (cola_power_spectrum's a_out) keep the standard drift. */
+#define COLA_FLAG_MODIFIED_KDK 4u
 
 #define COLA_PK_DECONV_CIC 1 /* divide each mode by W_CIC(k)^2 (Sec. 2.5) */
 #define COLA_PK_ALIAS_JING 2 /* divide by prod_i [1 - 2/3 sin^2(pi n_i/ng)] (Jing 2005, Sec. 2.5) */
@@ -377,6 +385,11 @@ int32_t cola_num_kernel_ids(void);
 const char* cola_kernel_name(int32_t id);
 
 const char* cola_strerror(int code);
+
+/* The CUDA runtime's description of the error behind the most recent
+ * COLA_ECUDA that a kernel launch or a shared-memory attribute call returned
+ * (process-wide; "no error" if there was none).  A diagnostic aid only. */
+const char* cola_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

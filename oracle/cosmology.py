@@ -230,6 +230,34 @@ def drift_integral(a: float, b: float, c: Cosmology) -> float:
     return val
 
 
+# Modified kick and drift factors of Tassev, Zaldarriaga & Eisenstein (2013),
+# the COLA paper the ICE-COLA paper cites for the method (Sec. 1, Eq. 2).
+# With p = a^2 dx/dt, dx/da = p / (a^3 E) and dp/da = F / (a E):
+# * the standard factors take F constant over a kick and p constant over a
+#   drift (kick_integral, drift_integral);
+# * the modified ones take the residual momentum to vary as a power of a,
+#   a^n with n = n_LPT, about the reference time a_c at which the force, or
+#   the momentum, is known:
+#     kick:  p(a) = alpha + beta a^n with dp/da(a_c) = F(a_c) / (a_c E(a_c))
+#            -> Delta p = F(a_c) (a_f^n - a_i^n) / (n a_c^n E(a_c))
+#     drift: p(a) = p(a_c) (a / a_c)^n
+#            -> Delta x = p(a_c) a_c^-n int_{a_i}^{a_f} a^n / (a^3 E) da
+# n_LPT = -2.5 is the value that paper adopts.  The reading of their
+# definitions in these variables is this module's.
+N_LPT = -2.5
+
+
+def kick_modified(a: float, b: float, ac: float, c: Cosmology, n: float = N_LPT) -> float:
+    """Modified kick factor from a to b, reference time ac (force at ac)."""
+    return (b**n - a**n) / (n * ac**n * float(E(ac, c)))
+
+
+def drift_modified(a: float, b: float, ac: float, c: Cosmology, n: float = N_LPT) -> float:
+    """Modified drift factor from a to b, reference time ac (momentum at ac)."""
+    val, _ = integrate.quad(lambda t: t**n / (t**3 * float(E(t, c))), a, b, epsabs=0.0, epsrel=1e-13)
+    return val / ac**n
+
+
 def time_nodes(a_i: float, a_f: float, n: int, sampling="linear", p: float = 1.0):
     """Eq. 3: n nodes with constant Delta f = (f(a_f) - f(a_i)) / (n - 1).
 
@@ -272,7 +300,11 @@ class StepTable:
     dD2da: np.ndarray
 
 
-def step_table(c: Cosmology, a_nodes, growth: Growth | None = None) -> StepTable:
+def step_table(c: Cosmology, a_nodes, growth: Growth | None = None, modified: bool = False,
+               n_lpt: float = N_LPT) -> StepTable:
+    """modified: the Tassev et al. (2013) kick and drift factors (kick about
+    the node a_j, drift about the midpoint a_{j+1/2} where the kicked momentum
+    sits); otherwise the standard ones."""
     a_nodes = np.asarray(a_nodes, dtype=np.float64)
     n = a_nodes.size
     g = growth if growth is not None else Growth(c)
@@ -283,11 +315,15 @@ def step_table(c: Cosmology, a_nodes, growth: Growth | None = None) -> StepTable
     dD1 = np.zeros(n)
     dD2 = np.zeros(n)
     for j in range(n):
+        aj = a_nodes[j]
         if j > 0:
-            kick[j] += kick_integral(0.5 * (a_nodes[j - 1] + a_nodes[j]), a_nodes[j], c)
+            am = 0.5 * (a_nodes[j - 1] + aj)
+            kick[j] += kick_modified(am, aj, aj, c, n_lpt) if modified else kick_integral(am, aj, c)
         if j < n - 1:
-            kick[j] += kick_integral(a_nodes[j], 0.5 * (a_nodes[j] + a_nodes[j + 1]), c)
-            drift[j] = drift_integral(a_nodes[j], a_nodes[j + 1], c)
+            ap = 0.5 * (aj + a_nodes[j + 1])
+            kick[j] += kick_modified(aj, ap, aj, c, n_lpt) if modified else kick_integral(aj, ap, c)
+            drift[j] = (drift_modified(aj, a_nodes[j + 1], ap, c, n_lpt) if modified
+                        else drift_integral(aj, a_nodes[j + 1], c))
             dD1[j] = D1[j + 1] - D1[j]
             dD2[j] = D2[j + 1] - D2[j]
     return StepTable(a=a_nodes, green=green, c1=green * D1, c2=green * (D2 - D1**2),

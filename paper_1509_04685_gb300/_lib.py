@@ -20,6 +20,7 @@ ERRORS = {-1: "COLA_EINVAL", -2: "COLA_EWORKSPACE", -3: "COLA_EUNSUPPORTED_SIZE"
 SAMPLING_LINEAR, SAMPLING_LOG, SAMPLING_POW = 0, 1, 2
 FLAG_PM_ONLY = 1
 FLAG_LEARNED = 2
+FLAG_MODIFIED_KDK = 4
 NET_NPARAMS = 9971
 NET_NPACK = 31104
 NET_OFFSETS = {"W1": (0, (16, 4, 27)), "b1": (1728, (16,)), "W2": (1744, (16, 16, 27)), "b2": (8656, (16,)),
@@ -54,7 +55,8 @@ class cola_state(ctypes.Structure):
 class ColaError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {ERRORS.get(code, code)} ({_strerror(code)})")
+        detail = f"; CUDA: {LIB.cola_last_cuda_error().decode()}" if code == -4 else ""
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({_strerror(code)}{detail})")
 
 
 def _load():
@@ -102,6 +104,7 @@ def _load():
         "cola_num_kernel_ids": ([], i32),
         "cola_kernel_name": ([i32], ctypes.c_char_p),
         "cola_fof_set_retry_cap": ([i32], ctypes.c_int),
+        "cola_last_cuda_error": ([], ctypes.c_char_p),
         "cola_checkpoint_bytes": ([cfgp, ctypes.POINTER(sz)], ctypes.c_int),
         "cola_checkpoint_save": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
         "cola_checkpoint_load": ([cfgp, vp, sz, stp, ctypes.POINTER(i32), vp], ctypes.c_int),

@@ -1,6 +1,7 @@
 // C ABI entry points (include/cola.h): argument checking, workspace layout and
 // the sequencing of the kernels of each call.  No allocation happens here:
 // every buffer lives in the caller's workspace or state arrays.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -38,8 +39,26 @@ static bool net_on(const cola_config* c) {
 bool layout_for(const cola_config* cfg, Layout* L) {
     const int ng = cfg->ng, nq = cfg->nq;
     const size_t Mg = mesh_bytes(ng), Mq = mesh_bytes(nq);
+    const size_t np = (size_t)nq * nq * nq, nb = (size_t)ng * ng;
     L->dep = align_up(kHdrBytes, 4096);
-    L->F = align_up(L->dep + (size_t)ng * ng * ng * 8, 4096);
+    // the step's bins and slots share the fixed-point region (never in use at the same time)
+    size_t o = L->dep;
+    L->bstart = o;
+    o = align_up(o + (nb + 1) * 4, 256);
+    L->bsums = o;
+    o = align_up(o + scan_sums_bytes((long long)nb) + 4, 256);
+    L->bkey = o;
+    o = align_up(o + np * 4, 256);
+    L->brank = o;
+    o = align_up(o + np * 4, 256);
+    L->bsorted = o;
+    o = align_up(o + np * 4, 256);
+    L->bcic = o;
+    o = align_up(o + np * 16, 256);
+    L->slots = o;
+    o = align_up(o + 12 * np * 4, 256);
+    const size_t dep_end = std::max(L->dep + (size_t)ng * ng * ng * 8, o);
+    L->F = align_up(dep_end, 4096);
     L->ic = L->dep;
     L->pk_part = align_up(L->F + 2 * Mg, 4096);
     size_t end = L->F + 3 * Mg;
@@ -84,29 +103,40 @@ static double host_node_a(const cola_config* c, int j) {
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// deposit + forward z, y passes + fused x/Green pass + inverse y, z passes on
-// the interleaved force mesh F (rows (ix, iy, c) of P complex): delta_k lives
-// in component 0 until the x pass replaces it by F_x and adds F_y, F_z; the
-// inverse y and z passes then run over all three components in one launch each.
+static BinBufs bin_bufs(void* ws, const Layout& L) {
+    return BinBufs{reinterpret_cast<int*>(wsp(ws, L.bstart)), reinterpret_cast<int*>(wsp(ws, L.bsums)),
+                   reinterpret_cast<int*>(wsp(ws, L.bkey)),   reinterpret_cast<int*>(wsp(ws, L.brank)),
+                   reinterpret_cast<int*>(wsp(ws, L.bsorted)), reinterpret_cast<float4*>(wsp(ws, L.bcic))};
+}
+static float* slots_ptr(void* ws, const Layout& L) { return reinterpret_cast<float*>(wsp(ws, L.slots)); }
+
+// The PM force of Sec. 2.2 on the interleaved force mesh F (rows (ix, iy, c)
+// of P complex): the particles are binned by mesh row; the r2c pass along z
+// deposits them row tile by row tile in shared memory and transforms the rows
+// (delta_k in component 0); y pass; the fused x pass (Green's function,
+// gradient) replaces delta_k by F_x and Psi; the inverse y pass gives the three
+// components.  The inverse z pass then either gathers the particles' partial
+// CIC sums into the slots (to_slots; *tx receives its tile width) or writes the
+// real force mesh (the learned net and the least-squares filter read it).
 static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
-                          cudaStream_t s, const float* filt = nullptr, int nfilt = 0, bool learned = false) {
+                          cudaStream_t s, const float* filt, int nfilt, bool learned, bool to_slots, int* tx) {
     const int ng = cfg->ng, nq = cfg->nq;
-    unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
     float2* F = reinterpret_cast<float2*>(wsp(ws, L.F));
     const float2* tw = twiddle_ptr(ws, kTwMesh);
     const double ratio = (double)ng / (double)nq;
     const float scale = (float)(ratio * ratio * ratio / 1099511627776.0);
     const double ng3 = (double)ng * ng * ng;
     const long long P = fft_pitch(ng), n2 = (long long)ng * ng;
+    const BinBufs bb = bin_bufs(ws, L);
+    const RowBins bins{bb.start, bb.sorted, bb.cic};
     int rc;
-    if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws), s)))
-        return rc;
+    if ((rc = launch_bins(st->d, nq, ng, cfg->box, bb, status_ptr(ws), s))) return rc;
     // the net's input keeps delta in real space (first buffer of the learned region)
-    if (learned && (rc = launch_fix_to_delta(dep, reinterpret_cast<float*>(wsp(ws, L.lrn)), ng, scale, s, false)))
+    if ((rc = fft_z_r2c_deposit(st->d, nq, bins, F, ng, cfg->box, scale, tw,
+                                learned ? reinterpret_cast<float*>(wsp(ws, L.lrn)) : nullptr, s)))
         return rc;
     const FRow fr = force_rows(ng);
     const long long XB = 1ll << fr.xbs;
-    if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, P, n2, fr))) return rc;
     // y lines of component 0 (outer x = xb XB + xi), then of all three components (outer 3 x + c)
     if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * XB * P, ng, (int)XB, 3 * XB * ng * P, 3 * P}, kKYFwd)))
         return rc;
@@ -117,6 +147,7 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
                           nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f, &psi)))
         return rc;
     if ((rc = fft_y_inverse_force(F, ng, tw, s, psi, kf))) return rc;
+    if (to_slots) return fft_z_c2r_gather(F, ng, st->d, nq, bins, slots_ptr(ws, L), cfg->box, tw, tx, s);
     if ((rc = fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2))) return rc;
     if (learned) return net_forward(cfg->net, wsp(ws, L.lrn), ng, nq, (float)green, F, s);
     return COLA_OK;
@@ -133,14 +164,20 @@ static const float* filter_row(const cola_config* cfg, double a) {
     return n->filter + (size_t)r * n->nfilter;
 }
 
+// The force of the configuration (plain, or with the learned filter and net).
+// With to_slots and no net, the forces end as partial sums in the slots
+// (*tx set); otherwise as the real force mesh (*tx = 0).
 static int pm_forces_for(const cola_config* cfg, const cola_state* st, double green, void* ws, const Layout& L,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool to_slots, int* tx) {
+    const bool net = net_on(cfg);
+    to_slots = to_slots && !net;
+    *tx = 0;
     if (cfg->flags & COLA_FLAG_LEARNED) {
         const double a = 1.5 * cfg->cosmo.omega_m / green;
         return pm_mesh_forces(cfg, st, green, ws, L, s, filter_row(cfg, a), cfg->net->filter ? cfg->net->nfilter : 0,
-                              net_on(cfg));
+                              net, to_slots, tx);
     }
-    return pm_mesh_forces(cfg, st, green, ws, L, s);
+    return pm_mesh_forces(cfg, st, green, ws, L, s, nullptr, 0, false, to_slots, tx);
 }
 
 static const float2* twiddles_for(int n, const cola_config* cfg, void* ws, cudaStream_t s, int* rc) {
@@ -162,12 +199,16 @@ int step_node(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
     if (rc) return rc;
     if (!state_ok(st, true) || step < 0 || step >= cfg->n_steps) return COLA_EINVAL;
     const double green = 1.5 * cfg->cosmo.omega_m / host_node_a(cfg, step);
-    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
+    int tx = 0;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s, true, &tx))) return rc;
     if (before_kick && cudaStreamWaitEvent(s, before_kick, 0) != cudaSuccess) return COLA_ECUDA;
-    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st,
-                                    table_ptr(ws) + (size_t)step * kTableCols, cfg->nq, cfg->ng, cfg->box,
-                                    step == cfg->n_steps - 1, (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
-                                    status_ptr(ws), s);
+    const double* row = table_ptr(ws) + (size_t)step * kTableCols;
+    const int last = step == cfg->n_steps - 1, pm_only = (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0;
+    if (tx)
+        return launch_slot_kick_drift(slots_ptr(ws, L), bin_bufs(ws, L).rank, *st, row, cfg->nq, last, pm_only,
+                                      status_ptr(ws), s);
+    return launch_gather_kick_drift(reinterpret_cast<float2*>(wsp(ws, L.F)), *st, row, cfg->nq, cfg->ng, cfg->box,
+                                    last, pm_only, status_ptr(ws), s);
 }
 
 }  // namespace cola
@@ -192,8 +233,6 @@ int cola_init(const cola_config* cfg, void* ws, size_t ws_bytes, void* stream) {
     if (rc) return rc;
     cudaStream_t s = S(stream);
     if (cudaMemsetAsync(ws, 0, kHdrBytes, s) != cudaSuccess) return COLA_ECUDA;
-    if (cudaMemsetAsync(wsp(ws, L.dep), 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess)
-        return COLA_ECUDA;
     if ((rc = launch_twiddles(twiddle_ptr(ws, kTwMesh), cfg->ng, s))) return rc;
     if ((rc = launch_twiddles(twiddle_ptr(ws, kTwLagr), cfg->nq, s))) return rc;
     return launch_tables(cfg, table_ptr(ws), s);
@@ -206,11 +245,7 @@ int cola_ic_2lpt(const cola_config* cfg, uint64_t seed, cola_state* st, void* ws
     if (!state_ok(st, true)) return COLA_EINVAL;
     if ((rc = cola_init(cfg, ws, ws_bytes, stream))) return rc;
     cudaStream_t s = S(stream);
-    if ((rc = launch_ic(cfg, seed, *st, ws, L, s))) return rc;
-    // the 2LPT scratch aliases the fixed-point mesh, which must be zero between calls
-    if (cudaMemsetAsync(wsp(ws, L.dep), 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess)
-        return COLA_ECUDA;
-    return COLA_OK;
+    return launch_ic(cfg, seed, *st, ws, L, s);
 }
 
 int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float* force, void* ws, size_t ws_bytes,
@@ -221,7 +256,9 @@ int cola_pm_force(const cola_config* cfg, const cola_state* st, double a, float*
     if (!state_ok(st, false) || !force || !(a > 0.0)) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / a;
-    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
+    int tx = 0;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s, true, &tx))) return rc;
+    if (tx) return launch_slot_force(slots_ptr(ws, L), bin_bufs(ws, L).rank, force, cfg->nq, s);
     return launch_gather(reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, force, cfg->nq, cfg->ng, cfg->box, s);
 }
 
@@ -257,6 +294,8 @@ static int power_common(const cola_config* cfg, const cola_state* st, int32_t no
     const float2* tw = twiddles_for(ng_pk, cfg, ws, s, &rc);
     if (rc) return rc;
     const double ratio = (double)ng_pk / (double)cfg->nq;
+    // the region is shared with the step's bins: start from zero counts (the z pass clears them again)
+    if (cudaMemsetAsync(dep, 0, (size_t)ng_pk * ng_pk * ng_pk * 8, s) != cudaSuccess) return COLA_ECUDA;
     if ((rc = launch_deposit_ex(st->d, st->v, st->psi1, st->psi2, dep, cfg->nq, ng_pk, cfg->box, snap,
                                 status_ptr(ws), s, rsd)))
         return rc;
@@ -294,6 +333,7 @@ int cola_density(const cola_config* cfg, const cola_state* st, float* delta, voi
     if (!state_ok(st, false) || !delta) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+    if (cudaMemsetAsync(dep, 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess) return COLA_ECUDA;
     if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, cfg->nq, cfg->ng, cfg->box, nullptr,
                                 status_ptr(ws), s)))
         return rc;
@@ -356,7 +396,8 @@ int cola_net_grad(const cola_config* cfg, const cola_state* st, double a, const 
     if (!net_on(cfg) || !state_ok(st, false) || !target || !grad || !loss || !(a > 0.0)) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     const double green = 1.5 * cfg->cosmo.omega_m / a;
-    if ((rc = pm_forces_for(cfg, st, green, ws, L, s))) return rc;
+    int tx = 0;
+    if ((rc = pm_forces_for(cfg, st, green, ws, L, s, false, &tx))) return rc;
     return net_backward(cfg->net, wsp(ws, L.lrn), cfg->ng, cfg->nq, cfg->box, (float)green,
                         reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, target, grad, loss, s);
 }
@@ -380,7 +421,8 @@ int cola_filter_accumulate(const cola_config* cfg, const cola_state* st, double 
     float* table = reinterpret_cast<float*>(wsp(ws, kHdrFilter));
     for (int b = 0; b < nb; ++b) {
         if ((rc = launch_basis_table(table, nb, b, s))) return rc;
-        if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s, table, nb, false))) return rc;
+        int tx = 0;
+        if ((rc = pm_mesh_forces(cfg, st, green, ws, L, s, table, nb, false, false, &tx))) return rc;
         if ((rc = launch_gather(reinterpret_cast<float2*>(wsp(ws, L.F)), st->d, basis + (size_t)b * np3, cfg->nq,
                                 cfg->ng, cfg->box, s)))
             return rc;
@@ -405,6 +447,10 @@ int cola_status(void* ws, size_t ws_bytes, void* stream) {
 }
 
 uint64_t cola_launch_count(void) { return g_launches; }
+
+const char* cola_last_cuda_error(void) {
+    return g_last_cuda_error ? cudaGetErrorString((cudaError_t)g_last_cuda_error) : "no error";
+}
 
 const char* cola_strerror(int code) {
     switch (code) {

@@ -10,6 +10,14 @@
 
 namespace cola {
 
+// Row bins of the PM step: particles sorted by the (x, y) mesh row of their
+// lower CIC corner, bin x ng + y holding sorted[start[b] .. start[b + 1]).
+struct RowBins {
+    const int* start;     // ng^2 + 1 offsets
+    const int* sorted;    // particle indices
+    const float4* cic;    // per sorted particle: CIC fractions (fx, fy, fz) and the lower z cell (int bits in w)
+};
+
 // ---------------------------------------------------------------------------
 // complex helpers (float2 = complex64)
 // ---------------------------------------------------------------------------
@@ -469,7 +477,9 @@ constexpr size_t kHdrBytes = 524288;
 enum TwSlot { kTwMesh = 0, kTwLagr = 1, kTwScratch = 2 };
 
 struct Layout {
-    size_t dep;        // uint64 fixed-point CIC mesh, ng^3 (zero between calls)
+    size_t dep;        // uint64 fixed-point CIC mesh, ng^3 (outputs and the density call; cleared by its user)
+    // the PM step's row bins and partial force sums, aliasing the region of dep
+    size_t bstart, bsums, bkey, brank, bsorted, bcic, slots;
     size_t F;          // interleaved force mesh: ng x ng x 3 rows of P complex (delta_k in component 0)
     size_t ic;         // 2LPT scratch: 7 complex meshes of nq x nq x Pq (aliases dep..)
     size_t pk_part;    // P(k) per-block partial sums (after the first two thirds of F)
@@ -524,7 +534,8 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // ---------------------------------------------------------------------------
 enum KernelId {
     kKDeposit = 0, kKZr2cFix, kKZr2c, kKYFwd, kKXFwd, kKXGreen, kKYInv, kKXInv, kKZc2r, kKGatherKD, kKGather,
-    kKFixToDelta, kKPkShells, kKPkReduce, kKIc, kKSetup, kKLearned, kNumKernelIds
+    kKFixToDelta, kKPkShells, kKPkReduce, kKIc, kKSetup, kKLearned, kKBins, kKDepR2c, kKC2rGather, kKKickDrift,
+    kNumKernelIds
 };
 // a ProfScope with id < 0 records nothing (launches inside an enclosing scope)
 class ProfScope {
@@ -540,9 +551,13 @@ class ProfScope {
 // host-side launch helpers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 extern unsigned long long g_launches;
+extern int g_last_cuda_error;  // the CUDA error behind the last COLA_ECUDA of a launch (cola_last_cuda_error)
 inline int check_launch() {
     g_launches++;
-    return cudaGetLastError() == cudaSuccess ? COLA_OK : COLA_ECUDA;
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return COLA_OK;
+    g_last_cuda_error = (int)e;
+    return COLA_ECUDA;
 }
 
 int launch_twiddles(float2* tw, int n, cudaStream_t s);
@@ -582,6 +597,36 @@ int launch_fix_to_delta(unsigned long long* dep, float* delta, int ng, float sca
 int launch_adjoint_deposit(const float* d, const float* res, unsigned long long* fix3, int nq, int ng, double box,
                            cudaStream_t s);
 int set_particle_traversal(int edge, int brick_k);  // traversal order of the particle kernels (pm.cu)
+
+// Row bins of the PM step (pm.cu): start[ng^2 + 1] (counts, then offsets),
+// sums (exclusive_scan scratch), key/rank/sorted[Np], cic[Np] (RowBins::cic).
+struct BinBufs {
+    int *start, *sums, *key, *rank, *sorted;
+    float4* cic;
+};
+int launch_bins(const float* d, int nq, int ng, double box, const BinBufs& b, int* status, cudaStream_t s);
+// kick + drift (and the force alone) from the partial-sum records of the
+// fused c2r pass: slots float[Np][12] by sorted position, pos[p] (the bins'
+// rank array after the scatter) the sorted position of particle p
+int launch_slot_kick_drift(const float* slots, const int* pos, cola_state st, const double* row, int nq, int last,
+                           int pm_only, int* status, cudaStream_t s);
+int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cudaStream_t s);
+
+// Fused z passes of the PM step (fft.cu, fft_fused.cuh):
+// fft_z_r2c_deposit: CIC deposit of the binned particles into shared memory,
+// row tile by row tile, and the r2c along z of those rows, written to
+// component 0 of the force mesh (rows frow(x, y, 0)); with delta_out, delta is
+// also written there unpadded (float[ng^3], C order).
+int fft_z_r2c_deposit(const float* d, int nq, const RowBins& bins, float2* F, int ng, double box, float scale,
+                      const float2* tw, float* delta_out, cudaStream_t s);
+// fft_z_c2r_gather: c2r along z of all three force components, row tile by
+// row tile in shared memory, and each binned particle's partial CIC sums from
+// those rows into slots; *tx receives the tile's x rows for the kick.
+int fft_z_c2r_gather(float2* F, int ng, const float* d, int nq, const RowBins& bins, float* slots, double box,
+                     const float2* tw, int* tx, cudaStream_t s);
+// exclusive scan of a[0..n) in place, a[n] = total; sums holds scan_sums_bytes(n) (scan.cu)
+int exclusive_scan(int* a, long long n, int* sums, cudaStream_t s);
+size_t scan_sums_bytes(long long n);
 // one COLA node; the kick waits for before_kick when given (api.cu)
 int step_node(const cola_config* cfg, cola_state* st, int32_t step, void* ws, size_t ws_bytes, cudaStream_t s,
               cudaEvent_t before_kick);

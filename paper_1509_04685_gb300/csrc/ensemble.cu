@@ -80,17 +80,15 @@ int cola_ensemble_create(int32_t n, const cola_config* cfgs, const uint64_t* see
             cudaStreamWaitEvent(st[l], ev[nstreams], 0);
             for (int i : lanes[l]) {
                 cola_state s = states[i];
-                if (step_from == 0) {
-                    if (cola_ic_2lpt(&cfgs[i], seeds[i], &s, ws[i], ws_bytes[i], st[l])) {
-                        fail(COLA_ECUDA);
-                        break;
-                    }
-                } else if (cola_init(&cfgs[i], ws[i], ws_bytes[i], st[l])) {
-                    fail(COLA_ECUDA);
+                // a member's own error code is passed on
+                const int r = step_from == 0 ? cola_ic_2lpt(&cfgs[i], seeds[i], &s, ws[i], ws_bytes[i], st[l])
+                                             : cola_init(&cfgs[i], ws[i], ws_bytes[i], st[l]);
+                if (r) {
+                    fail(r);
                     break;
                 }
                 for (int j = step_from; j < step_to && !rc; ++j)
-                    if (cola_step(&cfgs[i], &s, j, ws[i], ws_bytes[i], st[l])) fail(COLA_ECUDA);
+                    if (const int rs = cola_step(&cfgs[i], &s, j, ws[i], ws_bytes[i], st[l])) fail(rs);
             }
             cudaEventRecord(ev[l], st[l]);
             cudaStreamWaitEvent(origin, ev[l], 0);

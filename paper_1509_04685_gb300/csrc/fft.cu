@@ -6,13 +6,15 @@
 // 16), index (ix, iy, kz) at (ix*n + iy)*P + kz.  The real view of the same
 // buffer has rows of 2P floats, real value (ix, iy, z) at (ix*n + iy)*2P + z.
 // Forward passes run z (r2c), y, x; inverse passes x, y, z (c2r).
+#include <algorithm>
 #include <cmath>
 
-#include "fft_static.cuh"
+#include "fft_fused.cuh"
 
 namespace cola {
 
 unsigned long long g_launches = 0;
+int g_last_cuda_error = 0;
 
 bool make_plan(int n, FftPlan* p) {
     const StaticPlan sp = static_plan(n);
@@ -441,13 +443,20 @@ static int z_rows_per_block(int M) {
 // Raise a kernel's dynamic shared-memory limit once per size (also keeps the
 // attribute call out of stream captures after the first, uncaptured use).
 bool set_smem(const void* fn, size_t bytes) {
-    if (bytes <= 48 * 1024) return true;
+    // the 48 KB a launch may take without the attribute covers static and
+    // dynamic shared memory together; the kernels' static arrays stay far below 8 KB
+    if (bytes + 8 * 1024 <= 48 * 1024) return true;
     static const void* fns[64];
     static size_t done[64];
     static int nf = 0;
     for (int i = 0; i < nf; ++i)
         if (fns[i] == fn && done[i] >= bytes) return true;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = (int)e;
+        cudaGetLastError();
+        return false;
+    }
     for (int i = 0; i < nf; ++i)
         if (fns[i] == fn) {
             done[i] = bytes;
@@ -512,6 +521,136 @@ int fft_z_c2r(float2* data, int n, const float2* tw, cudaStream_t s, float* out,
         if (!set_smem((const void*)k_fft_z_c2r<false>, smem)) return COLA_ECUDA;
         k_fft_z_c2r<false><<<(unsigned)grid, T, smem, s>>>(data, n, rs, nrows, NR, plan, tw, nullptr, 0, 1.f);
     }
+    return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// fused z passes of the PM step, runtime forms (fft_fused.cuh has the layout
+// of the tiles and slots and the compile-time forms)
+// ---------------------------------------------------------------------------
+// fixed-point counts staged in shared memory (rows of n) -> packed complex
+// pairs of delta = count scale - 1
+struct SmemFixLoader {
+    const unsigned long long* cnt;
+    int n;
+    float scale;
+    template <int R>
+    __device__ __forceinline__ void load(int l, int i0, int di, float2* v) const {
+        const ulonglong2* x = reinterpret_cast<const ulonglong2*>(cnt + (size_t)l * n);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const ulonglong2 c = x[i0 + r * di];
+            v[r] = make_float2((float)c.x * scale - 1.0f, (float)c.y * scale - 1.0f);
+        }
+    }
+};
+
+// one tile of ty rows (x, y0 .. y0 + ty - 1) per block
+__global__ void k_fft_z_r2c_dep(const float* __restrict__ d, int nq, long long np, float inv_cell, RowBins bins,
+                                float2* out, int n, long long rs, int ty, float scale, FftPlan plan,
+                                const float2* __restrict__ tw, FastDiv m1div, FRow fr, float* __restrict__ delta_out) {
+    extern __shared__ float2 sm[];
+    __shared__ long long obase[64];
+    __shared__ int beg[kMaxTileBins], pre[kMaxTileBins + 1], bxy[kMaxTileBins];
+    const int M = n / 2;
+    const int ls = spad(M) + 1;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(sm);
+    float2* a = sm + ty * n;
+    float2* b = a + ty * ls;
+    const int tpx = n / ty;
+    const int x = blockIdx.x / tpx, y0 = (blockIdx.x - x * tpx) * ty;
+    for (int e = threadIdx.x; e < ty * n; e += blockDim.x) cnt[e] = 0ull;
+    if (threadIdx.x < ty) obase[threadIdx.x] = frow(x, y0 + threadIdx.x, 0, fr) * rs;
+    const int nb = 2 * (ty + 1);
+    const int total = tile_bins(
+        bins, nb, n, [&](int bb) { return (wrap(x - 1 + bb / (ty + 1), n) << 16) | wrap(y0 - 1 + bb % (ty + 1), n); },
+        beg, pre, bxy);
+    tile_deposit(bins, beg, pre, bxy, nb, total, n, x, y0, ty, cnt);
+    __syncthreads();
+    if (delta_out) {
+        float* o = delta_out + ((long long)x * n + y0) * n;
+        for (int e = threadIdx.x; e < ty * n; e += blockDim.x) o[e] = (float)cnt[e] * scale - 1.0f;
+    }
+    const FftGeom g{ty, ls, 1, false, 0, 2};
+    const float2* Z = fft_run_smem<-1, false>(SmemFixLoader{cnt, n, scale}, a, b, plan, g, tw);
+    for (int e = threadIdx.x; e < ty * (M + 1); e += blockDim.x) {
+        const int l = (int)fdiv((unsigned)e, m1div), k = e - l * (M + 1);
+        const float2 za = Z[l * ls + spad(k == M ? 0 : k)];
+        const float2 zb = cconj(Z[l * ls + spad(k == 0 ? 0 : M - k)]);
+        const float2 E = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y + zb.y));
+        const float2 D = csub(za, zb);
+        const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+        out[obase[l] + k] = cadd(E, cmul(__ldg(&tw[k]), O));
+    }
+}
+
+// one tile of the 3 tx force rows of x_first .. x_first + tx - 1 at one y per block
+__global__ void k_fft_z_c2r_gather(const float2* __restrict__ data, int n, long long rs, int tx, FftPlan plan,
+                                   const float2* __restrict__ tw, FRow fr, const float* __restrict__ d, int nq,
+                                   long long np, float inv_cell, RowBins bins, float* __restrict__ slots) {
+    extern __shared__ float2 sm[];
+    __shared__ int beg[kMaxTileBins], pre[kMaxTileBins + 1], bxy[kMaxTileBins];
+    const int M = n / 2;
+    const int ls = spad(M) + 1;
+    const int nr = 3 * tx;
+    float2* sb = sm + nr * ls;
+    const int xg = blockIdx.x / n, y = blockIdx.x - xg * n, x_first = xg * tx;
+    const long long row0 = frow(x_first, y, 0, fr);
+    const int nb = 2 * (tx + 1);
+    const int total = tile_bins(
+        bins, nb, n,
+        [&](int bb) { return (wrap(x_first - 1 + bb % (tx + 1), n) << 16) | wrap(y - 1 + bb / (tx + 1), n); }, beg,
+        pre, bxy);
+    const FftGeom g{nr, ls, 1, false, 0, 2};
+    const float2* Z = fft_run_smem<+1, false>(C2rLoader{data, rs, M, row0, row0 + nr, tw}, sm, sb, plan, g, tw);
+    tile_gather(bins, beg, pre, bxy, nb, total, np, n, x_first, tx, y, Z, ls, slots);
+}
+
+int fft_z_r2c_deposit(const float* d, int nq, const RowBins& bins, float2* F, int ng, double box, float scale,
+                      const float2* tw, float* delta_out, cudaStream_t s) {
+    FftPlan plan;
+    if (!make_plan(ng / 2, &plan)) return COLA_EUNSUPPORTED_SIZE;
+    const FRow fr = force_rows(ng);
+    const long long P = fft_pitch(ng);
+    const float inv_cell = (float)((double)ng / box);
+    ProfScope ps(kKDepR2c, s);
+    int rc = COLA_OK;
+    if (launch_z_r2c_dep_static(d, nq, inv_cell, bins, F, ng, P, scale, tw, fr, delta_out, s, &rc)) return rc;
+    const int M = ng / 2;
+    // rows per tile: a power of two dividing ng, at most the runtime z pass's
+    // rows per block and ng / 2 (the tile's 2 (ty + 1) bins stay distinct)
+    const int want = std::min(std::min(z_rows_per_block(M), 64), ng / 2);
+    int ty = 1;
+    while (2 * ty <= want && ng % (2 * ty) == 0) ty *= 2;
+    const size_t smem = (size_t)ty * ng * 8 + (size_t)2 * ty * (spad(M) + 1) * 8;
+    const int T = pass_threads(plan, ty);
+    const long long grid = (long long)ng * (ng / ty);
+    if (!set_smem((const void*)k_fft_z_r2c_dep, smem)) return COLA_ECUDA;
+    k_fft_z_r2c_dep<<<(unsigned)grid, T, smem, s>>>(d, nq, (long long)nq * nq * nq, inv_cell, bins, F, ng, P, ty,
+                                                     scale, plan, tw, make_fastdiv(M + 1), fr, delta_out);
+    return check_launch();
+}
+
+int fft_z_c2r_gather(float2* F, int ng, const float* d, int nq, const RowBins& bins, float* slots, double box,
+                     const float2* tw, int* tx, cudaStream_t s) {
+    FftPlan plan;
+    if (!make_plan(ng / 2, &plan)) return COLA_EUNSUPPORTED_SIZE;
+    const FRow fr = force_rows(ng);
+    const long long P = fft_pitch(ng);
+    const float inv_cell = (float)((double)ng / box);
+    ProfScope ps(kKC2rGather, s);
+    int rc = COLA_OK;
+    if (launch_z_c2r_gather_static(F, ng, P, tw, fr, d, nq, inv_cell, bins, slots, tx, s, &rc)) return rc;
+    // x rows per tile: divides the x-block of the force layout, at most 4 and ng / 2
+    int t = std::min(std::min(1 << fr.xbs, 4), ng / 2);
+    *tx = t;
+    const int M = ng / 2;
+    const size_t smem = (size_t)2 * 3 * t * (spad(M) + 1) * 8;
+    const int T = pass_threads(plan, 3 * t);
+    const long long grid = (long long)(ng / t) * ng;
+    if (!set_smem((const void*)k_fft_z_c2r_gather, smem)) return COLA_ECUDA;
+    k_fft_z_c2r_gather<<<(unsigned)grid, T, smem, s>>>(F, ng, P, t, plan, tw, fr, d, nq, (long long)nq * nq * nq,
+                                                        inv_cell, bins, slots);
     return check_launch();
 }
 

@@ -1,7 +1,7 @@
 // Specialised strided and fused x/Green passes (fft_static.cuh) for the large
 // meshes: 768^3, 1152^3, 1536^3 and 2304^3, the tile-width tables and the
 // specialised z passes.
-#include "fft_static.cuh"
+#include "fft_fused.cuh"
 
 namespace cola {
 
@@ -115,6 +115,50 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
 }
 
 
+
+// (n, rows per tile, threads, blocks per SM) of the fused r2c + deposit pass
+#define COLA_ZR2CD_SPECS(X) \
+    X(256, 16, 256, 1)      \
+    X(384, 8, 128, 1)       \
+    X(768, 8, 256, 2)       \
+    X(1152, 4, 256, 2)      \
+    X(1536, 4, 256, 2)      \
+    X(2304, 2, 256, 2)
+
+// (n, x rows per tile, threads, blocks per SM) of the fused c2r + gather pass
+#define COLA_ZC2RG_SPECS(X) \
+    X(256, 2, 128, 4)       \
+    X(384, 2, 128, 4)       \
+    X(768, 1, 256, 3)       \
+    X(1152, 1, 256, 3)      \
+    X(1536, 1, 256, 3)      \
+    X(2304, 1, 256, 2)
+
+bool launch_z_r2c_dep_static(const float* d, int nq, float inv_cell, const RowBins& bins, float2* out, int n,
+                             long long rs, float scale, const float2* tw, FRow fr, float* delta_out, cudaStream_t s,
+                             int* rc) {
+#define COLA_CASE(NN, RR, TT, MB)                                                                          \
+    if (n == NN) {                                                                                         \
+        *rc = run_z_r2c_dep<NN, RR, TT, MB>(d, nq, inv_cell, bins, out, rs, scale, tw, fr, delta_out, s); \
+        return true;                                                                                       \
+    }
+    COLA_ZR2CD_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return false;
+}
+
+bool launch_z_c2r_gather_static(float2* data, int n, long long rs, const float2* tw, FRow fr, const float* d, int nq,
+                                float inv_cell, const RowBins& bins, float* slots, int* tx, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, TX, TT, MB)                                                                       \
+    if (n == NN) {                                                                                      \
+        *tx = TX;                                                                                       \
+        *rc = run_z_c2r_gather<NN, TX, TT, MB>(data, rs, tw, fr, d, nq, inv_cell, bins, slots, s);     \
+        return true;                                                                                    \
+    }
+    COLA_ZC2RG_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return false;
+}
 
 bool launch_y_psi_static(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
                          const float2* tw, float kf, cudaStream_t s, int* rc) {

@@ -38,8 +38,9 @@ __device__ double E_of(double a, const CosmoD& c) {
 // D2'' + (2 + dlnE/dy) D2' = 3/2 Om(a) (D2 - D1^2)): u and w are constant in the
 // matter era, so RK4 in these variables is accurate with far fewer steps than
 // in D1, D2 themselves, which grow like a and a^2.  State s = (u, u', w, w',
-// K, Dr) with K = int dy / E and Dr = int dy / (a^2 E) over the current segment.
-__device__ void growth_rhs(double y, const double* s, double* ds, const CosmoD& c) {
+// K, Dr) with K = int dy / E and Dr = int dy a^kn / (a^2 E) over the current
+// segment (kn = 0: the standard drift; kn = n_LPT: the modified drift's integral).
+__device__ void growth_rhs(double y, const double* s, double* ds, const CosmoD& c, double kn) {
     const double a = exp(y);
     const double a2 = a * a, a3 = a2 * a;
     const double E2 = c.om / a3 + c.ok / a2 + c.ol;
@@ -51,7 +52,7 @@ __device__ void growth_rhs(double y, const double* s, double* ds, const CosmoD& 
     ds[2] = s[3];
     ds[3] = -(4.0 + fr) * s[3] - (4.0 + 2.0 * fr - 1.5 * oma) * s[2] - 1.5 * oma * s[0] * s[0];
     ds[4] = 1.0 / E;
-    ds[5] = 1.0 / (a2 * E);
+    ds[5] = (kn != 0.0 ? exp(kn * y) : 1.0) / (a2 * E);
 }
 
 // step bounds in y: from the start to the first output, and between outputs
@@ -59,7 +60,7 @@ constexpr double kHEarly = 1.0 / 64.0;
 constexpr double kHSeg = 1.0 / 256.0;
 
 // Advance s from y0 to y1 with RK4 steps of at most hmax.
-__device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c, double hmax) {
+__device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c, double hmax, double kn = 0.0) {
     const double span = y1 - y0;
     if (span <= 0.0) return;
     const int nstep = (int)ceil(span / hmax);
@@ -67,19 +68,20 @@ __device__ void rk4_to(double* s, double y0, double y1, const CosmoD& c, double 
     double k1[6], k2[6], k3[6], k4[6], t[6];
     double y = y0;
     for (int i = 0; i < nstep; ++i) {
-        growth_rhs(y, s, k1, c);
+        growth_rhs(y, s, k1, c, kn);
         for (int q = 0; q < 6; ++q) t[q] = s[q] + 0.5 * h * k1[q];
-        growth_rhs(y + 0.5 * h, t, k2, c);
+        growth_rhs(y + 0.5 * h, t, k2, c, kn);
         for (int q = 0; q < 6; ++q) t[q] = s[q] + 0.5 * h * k2[q];
-        growth_rhs(y + 0.5 * h, t, k3, c);
+        growth_rhs(y + 0.5 * h, t, k3, c, kn);
         for (int q = 0; q < 6; ++q) t[q] = s[q] + h * k3[q];
-        growth_rhs(y + h, t, k4, c);
+        growth_rhs(y + h, t, k4, c, kn);
         for (int q = 0; q < 6; ++q) s[q] += h / 6.0 * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
         y = (i + 1 == nstep) ? y1 : y + h;
     }
 }
 
 constexpr double kAEarly = 1e-5;
+constexpr double kNLpt = -2.5;  // n_LPT of the modified kick and drift (Tassev et al. 2013)
 
 // the Einstein-de Sitter modes at a = kAEarly: D1 = a, D2 = -3/7 a^2
 __device__ void growth_init(double* s) {
@@ -98,7 +100,14 @@ __device__ double node_a(int j, int n, double ai, double af, int sampling, doubl
 }
 
 // Table row j (12 doubles): a, green, c1, c2, kick, drift, dD1, dD2, D1, D2, dD1/da, dD2/da.
-__global__ void k_tables(double* tab, int n, double ai, double af, int sampling, double sp, CosmoD c, int pm_only) {
+// kn = 0: the standard kick and drift factors, kick = int da / (a E) over
+// [a_{j-1/2}, a_{j+1/2}] and drift = int da / (a^3 E) over [a_j, a_{j+1}].
+// kn = n_LPT: the modified factors of Tassev et al. (2013), the residual
+// momentum varying as a power a^n of the scale factor about the reference time:
+// kick = (a_{j+1/2}^n - a_{j-1/2}^n) / (n a_j^n E(a_j)) (force at the node),
+// drift = a_{j+1/2}^-n int da a^n / (a^3 E) over [a_j, a_{j+1}] (momentum at the midpoint).
+__global__ void k_tables(double* tab, int n, double ai, double af, int sampling, double sp, CosmoD c, int pm_only,
+                         double kn) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double s[6];
     growth_init(s);
@@ -106,7 +115,7 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
     for (int j = 0; j < n; ++j) {
         const double aj = node_a(j, n, ai, af, sampling, sp);
         const double yj = log(aj);
-        rk4_to(s, y, yj, c, j == 0 ? kHEarly : kHSeg);
+        rk4_to(s, y, yj, c, j == 0 ? kHEarly : kHSeg, kn);
         y = yj;
         double* r = tab + (size_t)j * kTableCols;
         r[0] = aj;
@@ -122,7 +131,7 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
         if (j + 1 < n) {
             const double an = node_a(j + 1, n, ai, af, sampling, sp);
             const double ym = log(0.5 * (aj + an));
-            rk4_to(s, y, ym, c, kHSeg);
+            rk4_to(s, y, ym, c, kHSeg, kn);
             y = ym;
             r[4] += s[4];  // a_j -> mid_j
             r[5] = s[5];
@@ -164,12 +173,28 @@ __global__ void k_tables(double* tab, int n, double ai, double af, int sampling,
         }
         if (pm_only) r[2] = r[3] = r[6] = r[7] = 0.0;
     }
+    if (kn != 0.0) {
+        for (int j = 0; j < n; ++j) {
+            double* r = tab + (size_t)j * kTableCols;
+            const double aj = r[0];
+            const double ajn = pow(aj, kn);
+            double k = 0.0;
+            if (j > 0) k += ajn - pow(0.5 * (tab[(size_t)(j - 1) * kTableCols] + aj), kn);
+            if (j + 1 < n) {
+                const double am = 0.5 * (aj + tab[(size_t)(j + 1) * kTableCols]);
+                k += pow(am, kn) - ajn;
+                r[5] /= pow(am, kn);
+            }
+            r[4] = k / (kn * ajn * E_of(aj, c));
+        }
+    }
 }
 
 int launch_tables(const cola_config* cfg, double* table, cudaStream_t s) {
     ProfScope ps(kKSetup, s);
     k_tables<<<1, 32, 0, s>>>(table, cfg->n_steps, cfg->a_init, cfg->a_final, cfg->sampling, cfg->sampling_p,
-                              cosmo_of(cfg), (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0);
+                              cosmo_of(cfg), (cfg->flags & COLA_FLAG_PM_ONLY) ? 1 : 0,
+                              (cfg->flags & COLA_FLAG_MODIFIED_KDK) ? kNLpt : 0.0);
     return check_launch();
 }
 

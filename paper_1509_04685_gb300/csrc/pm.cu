@@ -1,29 +1,12 @@
-// Particle side of the PM step (Sec. 2.2): CIC deposit onto the force mesh and
-// the fused CIC gather + COLA kick + drift in the frame comoving with the
-// 2LPT trajectories (Eqs. 1-2).
-//
-// Particle p = (i*nq + j)*nq + k sits at mesh coordinate
-//   u = (i, j, k) * ng/nq + 1/2 + d * ng/L      (periodic)
-// The Lagrangian part is formed exactly in integers, (i*2ng + nq)/(2nq), and
-// only the small displacement term is FP32, so the CIC fraction keeps FP32
-// precision for any mesh size.
-//
-// Deposit determinism: each particle's eight CIC weights are turned into
-// unsigned 64-bit fixed point with 2^40 per particle (the largest corner takes
-// the remainder so the eight sum to exactly 2^40) and added with integer
-// atomics, which commute: the mesh is bit-identical run to run.
-#include "cola_common.cuh"
+// Particle side of the PM step (Sec. 2.2): the row binning of the particles,
+// the CIC deposit onto a global fixed-point mesh (outputs and the density
+// call), the CIC gather, and the COLA kick + drift in the frame comoving with
+// the 2LPT trajectories (Eqs. 1-2), either fused with a gather from the force
+// mesh or from the per-particle partial sums the fused c2r pass leaves.
+// Particle positions, CIC corners and deposit weights: particles.cuh.
+#include "particles.cuh"
 
 namespace cola {
-
-constexpr float kFix = 1099511627776.0f;  // 2^40
-constexpr unsigned long long kFixU = 1ull << 40;
-
-struct Cic {
-    int c0[3];    // lower corner cell (wrapped)
-    int c1[3];    // upper corner cell (wrapped)
-    float f[3];   // fraction towards the upper corner
-};
 
 // --------------------------------------------------------------------------
 // Traversal order of the particle kernels.  A block of kTravThreads threads
@@ -120,26 +103,6 @@ __device__ __forceinline__ long long site_index(const int idx[3], int nq) {
     return ((long long)idx[0] * nq + idx[1]) * nq + idx[2];
 }
 
-__device__ __forceinline__ bool particle_cic(const int idx[3], int nq, int ng, float inv_cell, const float dx[3],
-                                             Cic& c) {
-    const long long den = 2ll * nq;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const long long num = (long long)idx[a] * 2 * ng + nq;
-        const long long base = num / den;
-        const float frac0 = (float)(num - base * den) / (float)den;
-        const float t = frac0 + dx[a] * inv_cell;
-        if (!(fabsf(t) < 1.0e7f)) return false;  // NaN, Inf or absurd displacement
-        const float fl = floorf(t);
-        c.f[a] = t - fl;
-        long long cell = (base + (long long)fl) % ng;
-        if (cell < 0) cell += ng;
-        c.c0[a] = (int)cell;
-        c.c1[a] = (cell + 1 == ng) ? 0 : (int)cell + 1;
-    }
-    return true;
-}
-
 // --------------------------------------------------------------------------
 // deposit (optionally drifting to an output time on the fly:
 // d_out = d + dr v + dD1 psi1 + dD2 psi2, coefficients in snap[0..2])
@@ -171,28 +134,18 @@ __global__ void k_deposit(const float* __restrict__ d, const float* __restrict__
         set_status(status, COLA_ENONFINITE);
         return;
     }
-    const float wx[2] = {1.f - c.f[0], c.f[0]};
-    const float wy[2] = {1.f - c.f[1], c.f[1]};
-    const float wz[2] = {1.f - c.f[2], c.f[2]};
-    const int mx = c.f[0] >= 0.5f, my = c.f[1] >= 0.5f, mz = c.f[2] >= 0.5f;
+    unsigned long long w[8];
+    cic_fix_weights(c, w);
     const int ix[2] = {c.c0[0], c.c1[0]};
     const int iy[2] = {c.c0[1], c.c1[1]};
     const int iz[2] = {c.c0[2], c.c1[2]};
-    unsigned long long rest = kFixU;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                if (a == mx && b == my && e == mz) continue;
-                const unsigned long long w = __float2ull_rn(wx[a] * wy[b] * wz[e] * kFix);
-                rest -= w;
-                const long long cell = ((long long)ix[a] * ng + iy[b]) * ng + iz[e];
-                atomicAdd(dep + cell, w);
-            }
-    const long long cell = ((long long)(mx ? ix[1] : ix[0]) * ng + (my ? iy[1] : iy[0])) * ng + (mz ? iz[1] : iz[0]);
-    atomicAdd(dep + cell, rest);
+            for (int e = 0; e < 2; ++e)
+                atomicAdd(dep + ((long long)ix[a] * ng + iy[b]) * ng + iz[e], w[4 * a + 2 * b + e]);
 }
 
 int launch_deposit_ex(const float* d, const float* v, const float* psi1, const float* psi2, unsigned long long* dep,
@@ -379,6 +332,154 @@ int launch_adjoint_deposit(const float* d, const float* res, unsigned long long*
     ProfScope ps(kKDeposit, s);
     k_adjoint_deposit<<<trav_grid(tv), kTravThreads, 0, s>>>(d, res, fix3, nq, ng, (float)((double)ng / box), np,
                                                                 tv);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// Row binning of the PM step: a counting sort of the particle indices by the
+// (x, y) mesh row of their lower CIC corner, key x ng + y.  k_bin_count takes
+// each particle's rank inside its bin with an atomic (counts start at zero),
+// exclusive_scan turns the counts into offsets, k_bin_scatter writes
+// sorted[start[key] + rank] = p and, at the same place, the particle's CIC
+// fractions and lower z cell (its x and y cells are the bin's), so that the
+// fused passes read one contiguous 16-byte record per particle visit; rank[p]
+// is then replaced by that sorted position (-1 for a particle left out).  The order inside a bin depends on the atomics
+// and changes no result: the fused deposit adds integers, and every particle's
+// partial force sums are its own.  A non-finite position latches
+// COLA_ENONFINITE and leaves the particle out of every bin.
+// --------------------------------------------------------------------------
+__global__ void k_bin_count(const float* __restrict__ d, int nq, int ng, float inv_cell, long long np,
+                            int* __restrict__ count, int* __restrict__ key, int* __restrict__ rank, int* status,
+                            Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
+    const float dx[3] = {d[p], d[np + p], d[2 * np + p]};
+    Cic c;
+    if (!particle_cic(idx, nq, ng, inv_cell, dx, c)) {
+        set_status(status, COLA_ENONFINITE);
+        key[p] = -1;
+        return;
+    }
+    const int k = c.c0[0] * ng + c.c0[1];
+    key[p] = k;
+    rank[p] = atomicAdd(count + k, 1);
+}
+
+__global__ void k_bin_scatter(const float* __restrict__ d, int nq, int ng, float inv_cell, long long np,
+                              const int* __restrict__ key, int* __restrict__ rank, const int* __restrict__ start,
+                              int* __restrict__ sorted, float4* __restrict__ cic, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
+    const int k = key[p];
+    if (k < 0) {
+        rank[p] = -1;
+        return;
+    }
+    const float dx[3] = {d[p], d[np + p], d[2 * np + p]};
+    Cic c;
+    particle_cic(idx, nq, ng, inv_cell, dx, c);  // finite: k_bin_count binned it
+    const int pos = start[k] + rank[p];
+    sorted[pos] = (int)p;
+    cic[pos] = make_float4(c.f[0], c.f[1], c.f[2], __int_as_float(c.c0[2]));
+    rank[p] = pos;
+}
+
+int launch_bins(const float* d, int nq, int ng, double box, const BinBufs& b, int* status, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const long long nb = (long long)ng * ng;
+    ProfScope ps(kKBins, s);
+    if (cudaMemsetAsync(b.start, 0, (size_t)(nb + 1) * sizeof(int), s) != cudaSuccess) return COLA_ECUDA;
+    const Trav tv = make_trav(nq);
+    k_bin_count<<<trav_grid(tv), kTravThreads, 0, s>>>(d, nq, ng, (float)((double)ng / box), np, b.start, b.key,
+                                                        b.rank, status, tv);
+    int rc = check_launch();
+    if (rc) return rc;
+    if ((rc = exclusive_scan(b.start, nb, b.sums, s))) return rc;
+    k_bin_scatter<<<trav_grid(tv), kTravThreads, 0, s>>>(d, nq, ng, (float)((double)ng / box), np, b.key, b.rank,
+                                                          b.start, b.sorted, b.cic, tv);
+    return check_launch();
+}
+
+// --------------------------------------------------------------------------
+// Kick + drift of node j from the partial force sums the fused c2r pass left
+// (record layout: fft_fused.cuh).  The record of particle p is at its sorted
+// position pos[p]: 12 floats S(dy, xs)[c] at 6 dy + 3 xs + c, every one of them
+// written in each step (zeros where a tile held both x rows), summed in one
+// fixed order:  F = (S(0,0) + S(0,1)) + (S(1,0) + S(1,1)),
+// then exactly the arithmetic of k_gather_kick_drift.  A particle the binning
+// left out (non-finite position, pos = -1) latches COLA_ENONFINITE and keeps its
+// state.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void record_force(const float4* __restrict__ rec, float F[3]) {
+    const float4 a = __ldg(rec), b = __ldg(rec + 1), c = __ldg(rec + 2);
+    // a = S00 x y z, S01 x | b = S01 y z, S10 x y | c = S10 z, S11 x y z
+    F[0] = (a.x + a.w) + (b.z + c.y);
+    F[1] = (a.y + b.x) + (b.w + c.z);
+    F[2] = (a.z + b.y) + (c.x + c.w);
+}
+
+__global__ void k_slot_kick_drift(const float* __restrict__ slots, const int* __restrict__ pos,
+                                  float* __restrict__ d, float* __restrict__ v, const float* __restrict__ psi1,
+                                  const float* __restrict__ psi2, const double* __restrict__ row, int nq,
+                                  long long np, int last, int pm_only, int* status, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
+    const int at = pos[p];
+    if (at < 0) {
+        set_status(status, COLA_ENONFINITE);
+        return;
+    }
+    const float c1 = (float)row[2], c2 = (float)row[3], kick = (float)row[4];
+    const float drift = (float)row[5], dD1 = (float)row[6], dD2 = (float)row[7];
+    float F[3];
+    record_force(reinterpret_cast<const float4*>(slots) + 3ll * at, F);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long q = a * np + p;
+        const float s1 = psi1[q], s2 = psi2[q];
+        const float acc = pm_only ? F[a] : F[a] - c1 * s1 - c2 * s2;
+        const float vn = v[q] + kick * acc;
+        v[q] = vn;
+        if (!last) d[q] = d[q] + (pm_only ? drift * vn : drift * vn + dD1 * s1 + dD2 * s2);
+    }
+}
+
+int launch_slot_kick_drift(const float* slots, const int* pos, cola_state st, const double* row, int nq, int last,
+                           int pm_only, int* status, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const Trav tv = make_trav(nq);
+    ProfScope ps(kKKickDrift, s);
+    k_slot_kick_drift<<<trav_grid(tv), kTravThreads, 0, s>>>(slots, pos, st.d, st.v, st.psi1, st.psi2, row, nq, np,
+                                                              last, pm_only, status, tv);
+    return check_launch();
+}
+
+// the force alone (cola_pm_force), NaN for a particle the binning left out
+__global__ void k_slot_force(const float* __restrict__ slots, const int* __restrict__ pos, float* __restrict__ out,
+                             int nq, long long np, Trav tv) {
+    int idx[3];
+    if (!trav_site(tv, idx)) return;
+    const long long p = site_index(idx, nq);
+    const int at = pos[p];
+    if (at < 0) {
+        out[p] = out[np + p] = out[2 * np + p] = __int_as_float(0x7fc00000);
+        return;
+    }
+    float F[3];
+    record_force(reinterpret_cast<const float4*>(slots) + 3ll * at, F);
+    out[p] = F[0];
+    out[np + p] = F[1];
+    out[2 * np + p] = F[2];
+}
+
+int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cudaStream_t s) {
+    const long long np = (long long)nq * nq * nq;
+    const Trav tv = make_trav(nq);
+    ProfScope ps(kKGather, s);
+    k_slot_force<<<trav_grid(tv), kTravThreads, 0, s>>>(slots, pos, out, nq, np, tv);
     return check_launch();
 }
 

@@ -17,7 +17,8 @@ size_t g_used = 0;
 const char* kNames[kNumKernelIds] = {"deposit",     "fft_z_r2c_fix", "fft_z_r2c", "fft_y_fwd",  "fft_x_fwd",
                                      "fft_x_green", "fft_y_inv",     "fft_x_inv", "fft_z_c2r",  "gather_kick_drift",
                                      "gather",      "fix_to_delta",  "pk_shells", "pk_reduce",  "ic",
-                                     "setup",       "learned"};
+                                     "setup",       "learned",       "bins",      "dep_r2c",    "c2r_gather",
+                                     "kick_drift"};
 }  // namespace
 
 ProfScope::ProfScope(int id, cudaStream_t s) : rec_(-1), s_(s) {

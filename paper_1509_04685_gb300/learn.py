@@ -1,8 +1,11 @@
 """Training and evaluation of the learned coarse-mesh force correction.
 
-Every arithmetic step runs in the library's kernels (PM forces, least-squares
-filter fit, convolution net forward/backward, Adam); this module only
-allocates buffers and sequences the calls.
+Every arithmetic step on particles and meshes runs in the library's kernels
+(PM forces, least-squares filter fit, convolution net forward/backward, Adam);
+this module allocates buffers and sequences the calls.  The one exception is
+the calibration of the fitted filter (calibrated_filter): a reshaping of its
+table of nfilter_a x nfilter values by two scalars, done with torch between
+training runs.  It is part of training, not of the PM step.
 
 Training data are generated by the method itself: plain COLA runs on a mesh
 PM_grid = m_fine times finer than the particle grid (the paper's 3x), whose
@@ -216,6 +219,22 @@ def golden_section(f, lo: float, hi: float, iters: int = 8):
     return (x1, f1) if f1 < f2 else (x2, f2)
 
 
+def boost_shape(na: int, nb: int, a_init: float = 0.05, a_final: float = 1.0, device="cpu") -> torch.Tensor:
+    """(na, nb) shape of the calibration boost: (a_r / a_final) min(k_b / k_Ny, 1)^2
+    for filter row r at a_r (rows spaced linearly from a_init to a_final) and
+    node b at k_b = b sqrt(3) k_Ny / (nb - 1); one row (na = 1) gets a_r / a_f = 1."""
+    kn = torch.arange(nb, dtype=torch.float64, device=device) * (np.sqrt(3.0) / (nb - 1))
+    ar = a_init + torch.arange(na, dtype=torch.float64, device=device) * ((a_final - a_init) / max(na - 1, 1))
+    rows = (ar / a_final) if na > 1 else torch.ones_like(ar)
+    return rows[:, None] * (torch.clamp(kn, max=1.0) ** 2)[None, :]
+
+
+def calibrated_filter(base: torch.Tensor, g: float, c: float, shape: torch.Tensor) -> torch.Tensor:
+    """T' = (1 + g (T - 1)) (1 + c shape): g scales the fitted filter's departure
+    from 1, c adds a boost that grows with k up to k_Ny and with a."""
+    return ((1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)).float()
+
+
 def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: float = 1.0, rounds: int = 2,
                      device="cuda", use_net: bool = True):
     """Fit the least-squares filter's outcome on the training seeds: with
@@ -227,15 +246,13 @@ def calibrate_filter(corr: LearnedCorrection, final, nq: int, box: float, kmax: 
     from fit_filter_runs, outputs in increasing a).  Returns (g, c)."""
     na, nb = corr.filter.shape
     base = corr.filter.clone()
-    kn = torch.arange(nb, dtype=torch.float64, device=corr.device) * (np.sqrt(3.0) / (nb - 1))  # k / k_Ny
-    ar = 0.05 + torch.arange(na, dtype=torch.float64, device=corr.device) * (0.95 / max(na - 1, 1))  # row a
     # the sub-cell clustering the boost stands in for grows with time: scale it by a_r / a_final
-    shape = (ar if na > 1 else torch.ones_like(ar))[:, None] * (torch.clamp(kn, max=1.0) ** 2)[None, :]
+    shape = boost_shape(na, nb, device=corr.device)
     cfg = corr.config(nq, box, use_net=use_net)
     sim = Simulation(cfg, device=device)
 
     def apply(g, c):
-        corr.filter.copy_(((1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)).float())
+        corr.filter.copy_(calibrated_filter(base, g, c, shape))
 
     def objective(g, c):
         apply(g, c)

@@ -56,7 +56,9 @@ def test_algorithmic_bytes_of_the_step_kernels():
     # the per-launch accounting of the kernel table at 512^3 / 1536^3 (GB)
     nq, ng = 512, 1536
     want = {"deposit": 30.60, "fft_z_r2c_fix": 72.50, "fft_y_fwd": 29.03, "fft_x_green": 43.54,
-            "fft_y_inv": 72.57, "fft_z_c2r": 87.03, "gather_kick_drift": 53.15}
+            "fft_y_inv": 72.57, "fft_z_c2r": 87.03, "gather_kick_drift": 53.15,
+            # the fused step: bins, deposit + r2c, c2r + gather into 48-byte records, kick + drift
+            "bins": 9.16, "dep_r2c": 17.20, "c2r_gather": 52.67, "kick_drift": 16.64}
     for k, gb in want.items():
         assert bench.algorithmic_bytes(k, nq, ng) / 1e9 == pytest.approx(gb, abs=0.01), k
     assert bench.algorithmic_bytes("not_a_kernel", nq, ng) == 0.0

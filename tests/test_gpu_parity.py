@@ -95,15 +95,17 @@ def test_fft_rejects_bad_sizes():
 
 
 # ---------------------------------------------------------------- tables ---
-@pytest.mark.parametrize("sampling,p", [(C.SAMPLING_LINEAR, 1.0), (C.SAMPLING_LOG, 1.0), (C.SAMPLING_POW, 0.8)])
-def test_step_table_vs_oracle(growth, sampling, p):
-    cfg = config(8, 16, 64.0, n_steps=12, a_init=1 / 40, sampling=sampling, sampling_p=p)
+@pytest.mark.parametrize("sampling,p,flags", [(C.SAMPLING_LINEAR, 1.0, 0), (C.SAMPLING_LOG, 1.0, 0),
+                                               (C.SAMPLING_POW, 0.8, 0), (C.SAMPLING_LINEAR, 1.0, C.FLAG_MODIFIED_KDK),
+                                               (C.SAMPLING_LOG, 1.0, C.FLAG_MODIFIED_KDK)])
+def test_step_table_vs_oracle(growth, sampling, p, flags):
+    cfg = config(8, 16, 64.0, n_steps=12, a_init=1 / 40, sampling=sampling, sampling_p=p, flags=flags)
     sim = C.Simulation(cfg)
     sim.init_tables()
     got = host(sim.table())
     name = {C.SAMPLING_LINEAR: "linear", C.SAMPLING_LOG: "log", C.SAMPLING_POW: "pow"}[sampling]
     a = cm.time_nodes(1 / 40, 1.0, 12, name, p)
-    t = cm.step_table(COSMO, a, growth)
+    t = cm.step_table(COSMO, a, growth, modified=bool(flags & C.FLAG_MODIFIED_KDK))
     for col, name in enumerate(C.TABLE_COLUMNS):
         ref = getattr(t, name)
         np.testing.assert_allclose(got[:, col], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max(), err_msg=name)
@@ -383,25 +385,27 @@ def test_redshift_space_multipoles_vs_oracle(pm_only, da, plin, growth):
 SAMPLINGS = {C.SAMPLING_LINEAR: "linear", C.SAMPLING_LOG: "log", C.SAMPLING_POW: "pow"}
 
 
-@pytest.mark.parametrize("sampling,p,a_init", [
-    (C.SAMPLING_LINEAR, 1.0, 0.05),      # the paper's optimal setup: 40 linear steps from z = 19
-    (C.SAMPLING_LOG, 1.0, 0.05),         # Sec. 4.2, Eq. 3 with f = ln a
-    (C.SAMPLING_POW, 0.5, 0.05),         # Sec. 4.2, f = a^p
-    (C.SAMPLING_POW, 0.8, 0.05),
-    (C.SAMPLING_LINEAR, 1.0, 0.1),       # Sec. 4.3: z_i = 9
-    (C.SAMPLING_LINEAR, 1.0, 1.0 / 40),  # z_i = 39
-    (C.SAMPLING_LINEAR, 1.0, 1.0 / 101), # z_i = 100
+@pytest.mark.parametrize("sampling,p,a_init,flags", [
+    (C.SAMPLING_LINEAR, 1.0, 0.05, 0),      # the paper's optimal setup: 40 linear steps from z = 19
+    (C.SAMPLING_LOG, 1.0, 0.05, 0),         # Sec. 4.2, Eq. 3 with f = ln a
+    (C.SAMPLING_POW, 0.5, 0.05, 0),         # Sec. 4.2, f = a^p
+    (C.SAMPLING_POW, 0.8, 0.05, 0),
+    (C.SAMPLING_LINEAR, 1.0, 0.1, 0),       # Sec. 4.3: z_i = 9
+    (C.SAMPLING_LINEAR, 1.0, 1.0 / 40, 0),  # z_i = 39
+    (C.SAMPLING_LINEAR, 1.0, 1.0 / 101, 0), # z_i = 100
+    (C.SAMPLING_LINEAR, 1.0, 0.05, C.FLAG_MODIFIED_KDK),  # Tassev et al. (2013) kick and drift
 ])
-def test_full_run_small_config_vs_oracle(sampling, p, a_init, plin, growth):
+def test_full_run_small_config_vs_oracle(sampling, p, a_init, flags, plin, growth):
     """32^3 particles on a 96^3 mesh, L = 128 Mpc/h, 40 steps to z = 0 with the
     paper's time samplings and initial redshifts."""
     nq, ng, L = 32, 96, 128.0
-    cfg = config(nq, ng, L, a_init=a_init, sampling=sampling, sampling_p=p)
+    cfg = config(nq, ng, L, a_init=a_init, sampling=sampling, sampling_p=p, flags=flags)
     sim = C.Simulation(cfg)
     sim.ic(seed=1)
     sim.run()
     assert sim.status() == 0
-    tab = cm.step_table(COSMO, cm.time_nodes(a_init, 1.0, 40, SAMPLINGS[sampling], p), growth)
+    tab = cm.step_table(COSMO, cm.time_nodes(a_init, 1.0, 40, SAMPLINGS[sampling], p), growth,
+                        modified=bool(flags & C.FLAG_MODIFIED_KDK))
     ref = _oracle_state(1, nq, L, plin, growth, a=a_init)
     ocola.run(ref, tab, nq, ng, L)
     dq = L / nq

@@ -49,3 +49,25 @@ def test_pk_deviation_is_the_mean_relative_difference_up_to_kmax():
     p_ref = np.array([1.0, 2.0, 4.0, 8.0])
     p = np.array([1.1, 1.8, 4.0, 100.0])
     assert learn.pk_deviation(k, p, p_ref, 1.0) == pytest.approx((0.1 + 0.1 + 0.0) / 3)
+
+
+def test_calibrated_filter_rule():
+    # T' = (1 + g (T - 1)) (1 + c shape): g = 1, c = 0 keeps the fitted filter;
+    # g = 0 flattens it to 1 before the boost; the boost shape is (a_r / a_f)
+    # min(k / k_Ny, 1)^2, zero at k = 0, held beyond k_Ny, growing with a
+    import torch
+
+    na, nb = 8, 16
+    base = 1.0 + 0.3 * torch.sin(torch.arange(na * nb, dtype=torch.float32)).reshape(na, nb)
+    shape = learn.boost_shape(na, nb)
+    torch.testing.assert_close(learn.calibrated_filter(base, 1.0, 0.0, shape), base)
+    torch.testing.assert_close(learn.calibrated_filter(base, 0.0, 0.5, shape), (1.0 + 0.5 * shape).float())
+    assert torch.all(shape[:, 0] == 0)
+    kn = np.arange(nb) * np.sqrt(3.0) / (nb - 1)
+    beyond = kn >= 1.0
+    np.testing.assert_allclose(shape[:, beyond].numpy(), shape[:, beyond][:, :1].numpy().repeat(beyond.sum(), 1))
+    np.testing.assert_allclose(shape[:, 4].numpy(), np.linspace(0.05, 1.0, na) * kn[4] ** 2, rtol=1e-12)
+    assert torch.all(learn.boost_shape(1, nb)[0] == torch.clamp(torch.tensor(kn), max=1.0) ** 2)
+    g, c = 1.4, 0.2
+    want = (1.0 + g * (base.double() - 1.0)) * (1.0 + c * shape)
+    torch.testing.assert_close(learn.calibrated_filter(base, g, c, shape), want.float())
