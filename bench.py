@@ -101,6 +101,13 @@ def ensemble_members():
 def run_ensemble(args, rank, world, C, torch, dist):
     """One timed step = one graph launch replaying the 2LPT set-up and all 40
     nodes of this rank's members (members i = rank mod world)."""
+    line = ensemble_line(C, torch, dist, rank, world, max(1, args.warmup // 3), max(1, args.steps // 12))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def ensemble_line(C, torch, dist, rank, world, warmup, nrep):
+    """The ensemble's JSON line (see run_ensemble)."""
     mem = members_of(rank, world)
     cfgs = [C.make_config(nq, ng, box, A_INIT, 1.0, N_NODES) for nq, ng, box, _ in mem]
     sims = [C.Simulation(c) for c in cfgs]
@@ -119,7 +126,7 @@ def run_ensemble(args, rank, world, C, torch, dist):
         sm.ic(seed)
         sm.step(0)
     ens = C.Ensemble(cfgs, [m[3] for m in mem], [sm.state for sm in sims], [sm.ws for sm in sims], nstreams=8)
-    for _ in range(max(1, args.warmup // 3)):
+    for _ in range(warmup):
         ens.launch()
     torch.cuda.synchronize()
     if dist:
@@ -127,7 +134,6 @@ def run_ensemble(args, rank, world, C, torch, dist):
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     launches0 = C.cola_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nrep = max(1, args.steps // 12)
     e0.record()
     for _ in range(nrep):
         ens.launch()
@@ -139,18 +145,20 @@ def run_ensemble(args, rank, world, C, torch, dist):
         if sm.status() != 0:
             raise SystemExit("device status after ensemble")
     value, ms = replica_value(float(sum(nq**3 for nq, _, _, _ in mem) * N_NODES * nrep), ms, dist)
-    if rank == 0:
-        print(json.dumps({
-            "metric": "particle-steps/s (48-seed uneven ensemble, one CUDA-graph launch per run)", "value": value,
-            "unit": UNIT, "n_gpus": world, "steps": nrep, "warmup": max(1, args.warmup // 3),
-            "ms_per_step": ms / nrep, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["ensemble"]["name"], "members": 48, "n_steps": N_NODES,
-                       "step": "one graph launch = 2LPT set-up + 40 nodes of every member",
-                       "autotuned_tiles": {str(k): v for k, v in sorted(tuned.items())},
-                       "parallelism": f"members sharded over {world} rank(s)"},
-            "clocks": clk, "gpu_launches": C.cola_launch_count() - launches0,
-        }), flush=True)
+    launches = C.cola_launch_count() - launches0
+    del ens, sims
+    torch.cuda.empty_cache()
+    return {
+        "metric": "particle-steps/s (48-seed uneven ensemble, one CUDA-graph launch per run)", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": nrep, "warmup": warmup,
+        "ms_per_step": ms / nrep, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["ensemble"]["name"], "members": 48, "n_steps": N_NODES,
+                   "step": "one graph launch = 2LPT set-up + 40 nodes of every member",
+                   "autotuned_tiles": {str(k): v for k, v in sorted(tuned.items())},
+                   "parallelism": f"members sharded over {world} rank(s)"},
+        "clocks": clk, "gpu_launches": launches,
+    }
 def learned_study(C, torch, nq, box, train_seeds, test_seeds, net_iters, dev_index=0):
     """The learned 1x-mesh form against the plain 3x-mesh form (config 4 at
     nq = 256, L = 512 Mpc/h, 40 steps).  The radial filter is fitted by least
@@ -624,6 +632,7 @@ def main():
     ap.add_argument("--learned-iters", type=int, default=0,
                     help="Adam iterations of the convolution net (learned workload; 0: the filter alone)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-form summary of the default line")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ensemble summary of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -762,6 +771,20 @@ def main():
                        "train_seeds": 8, "test_seeds": 4, "training_s": st["training"]["seconds"]}
         except Exception as e:  # the headline stands without it
             learned = {"error": f"{type(e).__name__}: {e}"}
+    # config 3 alongside the headline at N = 1: one run of the 48-member ensemble
+    # (one graph launch; its own warm-up launch first)
+    ensemble = None
+    if world == 1 and args.workload == "full" and not args.no_ensemble:
+        if learned is None:
+            del sim, hst, host_state
+        torch.cuda.empty_cache()
+        try:
+            e = ensemble_line(C, torch, None, 0, 1, 1, 1)
+            ensemble = {"workload": e["config"]["workload"], "value": e["value"], "unit": e["unit"],
+                        "ms_per_run": e["ms_per_step"], "runs": e["steps"], "members": 48, "n_steps": N_NODES,
+                        "clocks": e["clocks"], "gpu_launches": e["gpu_launches"]}
+        except Exception as e:  # the headline stands without it
+            ensemble = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         line = {
@@ -788,6 +811,8 @@ def main():
         }
         if learned is not None:
             line["learned_1x"] = learned
+        if ensemble is not None:
+            line["ensemble"] = ensemble
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -45,6 +45,7 @@ extern "C" {
 #define COLA_ECUDA (-4)             /* a CUDA launch or runtime call failed */
 #define COLA_ETIMEOUT (-5)          /* a bounded device-side wait gave up */
 #define COLA_ENONFINITE (-6)        /* a kernel met a NaN/Inf in its input */
+#define COLA_EBOUNDS (-7)           /* a device bounds check failed (COLA_CHECKS builds only) */
 
 #define COLA_SAMPLING_LINEAR 0 /* Eq. 3 with f(a) = a (the paper's choice, Sec. 4.2) */
 #define COLA_SAMPLING_LOG 1    /* f(a) = ln a */
@@ -390,6 +391,26 @@ const char* cola_strerror(int code);
  * COLA_ECUDA that a kernel launch or a shared-memory attribute call returned
  * (process-wide; "no error" if there was none).  A diagnostic aid only. */
 const char* cola_last_cuda_error(void);
+
+/* 1 if this library was built with COLA_CHECKS defined, else 0.  In that build
+ * every data-dependent index of the PM step (the bin key of a particle's CIC
+ * row, its sorted position from the bin scan as the scatter, the fused z
+ * passes and the kick use it, the z cell stored in its CIC record) is checked
+ * before the access it guards; a failed check skips the access and latches
+ * COLA_EBOUNDS in the workspace's status word (read by cola_status).  The
+ * checks replace a memory checker where none can run; results are
+ * bit-identical to the normal build's. */
+int cola_checks_enabled(void);
+
+/* Test hook of the bounds checks: one device thread checks index < n and, if
+ * the check passes, writes one int at position `index` of a 64-int probe area
+ * in the workspace header.  COLA_EINVAL unless 1 <= n <= 64 and
+ * 0 <= index < 64 (so the write always stays inside the probe area).  In a
+ * COLA_CHECKS build an index >= n is caught on the device (the write is
+ * skipped, COLA_EBOUNDS latched); in the normal build it is refused on the
+ * host with COLA_EINVAL.  Asynchronous on `stream`; read the result with
+ * cola_status. */
+int cola_checks_probe(int32_t index, int32_t n, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

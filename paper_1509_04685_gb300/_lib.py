@@ -12,11 +12,14 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libcola_gb300.so")
+# COLA_GB300_CHECKS=1 loads the build with device bounds checks (build(checks=True))
+CHECKS = os.environ.get("COLA_GB300_CHECKS", "0") == "1"
+LIB_PATH = (os.path.join(_HERE, "_build_checks", "libcola_gb300_checks.so") if CHECKS else
+            os.path.join(_HERE, "_build", "libcola_gb300.so"))
 
 COLA_OK = 0
 ERRORS = {-1: "COLA_EINVAL", -2: "COLA_EWORKSPACE", -3: "COLA_EUNSUPPORTED_SIZE", -4: "COLA_ECUDA",
-          -5: "COLA_ETIMEOUT", -6: "COLA_ENONFINITE"}
+          -5: "COLA_ETIMEOUT", -6: "COLA_ENONFINITE", -7: "COLA_EBOUNDS"}
 SAMPLING_LINEAR, SAMPLING_LOG, SAMPLING_POW = 0, 1, 2
 FLAG_PM_ONLY = 1
 FLAG_LEARNED = 2
@@ -61,7 +64,8 @@ class ColaError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"COLA CUDA library not built ({LIB_PATH}); run paper_1509_04685_gb300.build.build()")
+        raise ImportError(f"COLA CUDA library not built ({LIB_PATH}); run paper_1509_04685_gb300.build.build"
+                          f"({'checks=True' if CHECKS else ''})")
     lib = ctypes.CDLL(LIB_PATH)
     vp, sz, i32, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double
     cfgp, stp = ctypes.POINTER(cola_config), ctypes.POINTER(cola_state)
@@ -108,6 +112,8 @@ def _load():
         "cola_checkpoint_bytes": ([cfgp, ctypes.POINTER(sz)], ctypes.c_int),
         "cola_checkpoint_save": ([cfgp, stp, i32, vp, sz, vp], ctypes.c_int),
         "cola_checkpoint_load": ([cfgp, vp, sz, stp, ctypes.POINTER(i32), vp], ctypes.c_int),
+        "cola_checks_enabled": ([], ctypes.c_int),
+        "cola_checks_probe": ([i32, i32, vp, sz, vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

@@ -128,7 +128,7 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     const double ng3 = (double)ng * ng * ng;
     const long long P = fft_pitch(ng), n2 = (long long)ng * ng;
     const BinBufs bb = bin_bufs(ws, L);
-    const RowBins bins{bb.start, bb.sorted, bb.cic};
+    const RowBins bins{bb.start, bb.sorted, bb.cic, status_ptr(ws), (long long)nq * nq * nq, ng};
     int rc;
     if ((rc = launch_bins(st->d, nq, ng, cfg->box, bb, status_ptr(ws), s))) return rc;
     // the net's input keeps delta in real space (first buffer of the learned region)
@@ -448,6 +448,17 @@ int cola_status(void* ws, size_t ws_bytes, void* stream) {
 
 uint64_t cola_launch_count(void) { return g_launches; }
 
+int cola_checks_enabled(void) { return kChecks ? 1 : 0; }
+
+int cola_checks_probe(int32_t index, int32_t n, void* ws, size_t ws_bytes, void* stream) {
+    if (!ws || ws_bytes < kHdrBytes || n < 1 || n > kProbeInts || index < 0 || index >= kProbeInts)
+        return COLA_EINVAL;
+    // without the device checks an index >= n is refused here; the write stays
+    // inside the probe area of the header in either build
+    if (!kChecks && index >= n) return COLA_EINVAL;
+    return launch_checks_probe(reinterpret_cast<int*>(wsp(ws, kHdrProbe)), index, n, status_ptr(ws), S(stream));
+}
+
 const char* cola_last_cuda_error(void) {
     return g_last_cuda_error ? cudaGetErrorString((cudaError_t)g_last_cuda_error) : "no error";
 }
@@ -461,6 +472,7 @@ const char* cola_strerror(int code) {
         case COLA_ECUDA: return "CUDA launch or runtime error";
         case COLA_ETIMEOUT: return "a bounded device wait gave up";
         case COLA_ENONFINITE: return "non-finite or out-of-range particle data";
+        case COLA_EBOUNDS: return "an index failed its bounds check (COLA_CHECKS build)";
         default: return "unknown error";
     }
 }

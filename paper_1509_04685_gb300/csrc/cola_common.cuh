@@ -16,6 +16,9 @@ struct RowBins {
     const int* start;     // ng^2 + 1 offsets
     const int* sorted;    // particle indices
     const float4* cic;    // per sorted particle: CIC fractions (fx, fy, fz) and the lower z cell (int bits in w)
+    int* status;          // the workspace's status word (bounds checks of a COLA_CHECKS build)
+    long long np;         // particles (sorted positions are < np)
+    int ng;               // mesh side (z cells are < ng)
 };
 
 // ---------------------------------------------------------------------------
@@ -468,7 +471,8 @@ constexpr int kTableCols = 12;
 constexpr size_t kHdrStatus = 0;          // int: latched device status
 constexpr size_t kHdrSigmaAmp = 64;       // double: P(k) amplitude A (sigma8 normalisation)
 constexpr size_t kHdrSnap = 128;          // 6 doubles: snapshot drift (dr, dD1, dD2), redshift-space (cv, c1, c2)
-constexpr size_t kHdrGrowthScratch = 256; // small FP64 scratch for the snapshot growth call
+constexpr size_t kHdrProbe = 512;         // 64 ints written by cola_checks_probe
+constexpr int kProbeInts = 64;
 constexpr size_t kHdrFilter = 1024;       // radial filter basis table (<= 64 floats)
 constexpr size_t kHdrTable = 4096;        // kMaxSteps x kTableCols doubles
 constexpr size_t kHdrTwiddle = 262144;    // 3 slots of kMaxFft float2
@@ -528,6 +532,21 @@ __device__ __forceinline__ void tile_prefetch(float2* stg, const float2* g, int 
 
 // device status latch
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Bounds check of a data-dependent index (a sorted position from the bin scan,
+// a z cell read back from a CIC record, a bin key).  In a build with
+// COLA_CHECKS defined a failed check latches COLA_EBOUNDS and the caller skips
+// the access; in the normal build the check is constant true and compiles away.
+#ifdef COLA_CHECKS
+constexpr bool kChecks = true;
+__device__ __forceinline__ bool bounds_ok(int* status, bool ok) {
+    if (!ok) set_status(status, COLA_EBOUNDS);
+    return ok;
+}
+#else
+constexpr bool kChecks = false;
+__device__ __forceinline__ bool bounds_ok(int*, bool) { return true; }
+#endif
 
 // ---------------------------------------------------------------------------
 // per-kernel event timing (prof.cu): a ProfScope around each launch
@@ -611,6 +630,8 @@ int launch_bins(const float* d, int nq, int ng, double box, const BinBufs& b, in
 int launch_slot_kick_drift(const float* slots, const int* pos, cola_state st, const double* row, int nq, int last,
                            int pm_only, int* status, cudaStream_t s);
 int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cudaStream_t s);
+// cola_checks_probe's kernel: area[index] = index if the bounds check index < n passes
+int launch_checks_probe(int* area, int index, int n, int* status, cudaStream_t s);
 
 // Fused z passes of the PM step (fft.cu, fft_fused.cuh):
 // fft_z_r2c_deposit: CIC deposit of the binned particles into shared memory,

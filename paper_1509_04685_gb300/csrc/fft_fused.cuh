@@ -114,10 +114,12 @@ __device__ __forceinline__ TilePart tile_load(int e, int total, const RowBins& b
     if (e < total) {
         const int b = tile_find(pre, nb, e);
         const int pos = beg[b] + (e - pre[b]);
+        if (!bounds_ok(bins.status, pos >= 0 && pos < bins.np)) return t;
         t.p = __ldg(bins.sorted + pos);
         t.q = __ldg(bins.cic + pos);
         t.b = b;
         t.pos = pos;
+        if (kChecks && !bounds_ok(bins.status, (unsigned)__float_as_int(t.q.w) < (unsigned)bins.ng)) t.p = -1;
     }
     return t;
 }

@@ -362,13 +362,17 @@ __global__ void k_bin_count(const float* __restrict__ d, int nq, int ng, float i
         return;
     }
     const int k = c.c0[0] * ng + c.c0[1];
+    if (!bounds_ok(status, (unsigned)k < (unsigned)(ng * ng))) {
+        key[p] = -1;
+        return;
+    }
     key[p] = k;
     rank[p] = atomicAdd(count + k, 1);
 }
 
 __global__ void k_bin_scatter(const float* __restrict__ d, int nq, int ng, float inv_cell, long long np,
                               const int* __restrict__ key, int* __restrict__ rank, const int* __restrict__ start,
-                              int* __restrict__ sorted, float4* __restrict__ cic, Trav tv) {
+                              int* __restrict__ sorted, float4* __restrict__ cic, int* status, Trav tv) {
     int idx[3];
     if (!trav_site(tv, idx)) return;
     const long long p = site_index(idx, nq);
@@ -381,6 +385,10 @@ __global__ void k_bin_scatter(const float* __restrict__ d, int nq, int ng, float
     Cic c;
     particle_cic(idx, nq, ng, inv_cell, dx, c);  // finite: k_bin_count binned it
     const int pos = start[k] + rank[p];
+    if (!bounds_ok(status, pos >= 0 && pos < np)) {
+        rank[p] = -1;
+        return;
+    }
     sorted[pos] = (int)p;
     cic[pos] = make_float4(c.f[0], c.f[1], c.f[2], __int_as_float(c.c0[2]));
     rank[p] = pos;
@@ -398,7 +406,7 @@ int launch_bins(const float* d, int nq, int ng, double box, const BinBufs& b, in
     if (rc) return rc;
     if ((rc = exclusive_scan(b.start, nb, b.sums, s))) return rc;
     k_bin_scatter<<<trav_grid(tv), kTravThreads, 0, s>>>(d, nq, ng, (float)((double)ng / box), np, b.key, b.rank,
-                                                          b.start, b.sorted, b.cic, tv);
+                                                          b.start, b.sorted, b.cic, status, tv);
     return check_launch();
 }
 
@@ -432,6 +440,7 @@ __global__ void k_slot_kick_drift(const float* __restrict__ slots, const int* __
         set_status(status, COLA_ENONFINITE);
         return;
     }
+    if (!bounds_ok(status, at < np)) return;
     const float c1 = (float)row[2], c2 = (float)row[3], kick = (float)row[4];
     const float drift = (float)row[5], dD1 = (float)row[6], dD2 = (float)row[7];
     float F[3];
@@ -480,6 +489,16 @@ int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cu
     const Trav tv = make_trav(nq);
     ProfScope ps(kKGather, s);
     k_slot_force<<<trav_grid(tv), kTravThreads, 0, s>>>(slots, pos, out, nq, np, tv);
+    return check_launch();
+}
+
+// one thread: the bounds check of index < n, then the write it guards
+__global__ void k_checks_probe(int* area, int index, int n, int* status) {
+    if (bounds_ok(status, index < n)) area[index] = index;
+}
+
+int launch_checks_probe(int* area, int index, int n, int* status, cudaStream_t s) {
+    k_checks_probe<<<1, 1, 0, s>>>(area, index, n, status);
     return check_launch();
 }
 

@@ -158,3 +158,15 @@ def test_checkpoint_size_and_header_checks_without_copying():
     assert L.cola_checkpoint_save(ctypes.byref(cfg), ctypes.byref(st), 3, p, n - 1, None) == -1  # short buffer
     assert L.cola_checkpoint_load(ctypes.byref(cfg), p, n - 1, ctypes.byref(st), ctypes.byref(node), None) == -1
     assert node.value == -1
+
+
+def test_checks_entry_points_without_launching():
+    # the product build carries no device bounds checks; the probe hook refuses
+    # anything outside its 64-int area before launching
+    import paper_1509_04685_gb300 as C
+    assert C.LIB.cola_checks_enabled() == 0
+    for index, n in ((-1, 8), (64, 64), (3, 0), (3, 65), (8, 8)):
+        assert C.LIB.cola_checks_probe(index, n, 1 << 20, 1 << 20, None) == -1
+    assert C.LIB.cola_checks_probe(0, 8, None, 1 << 20, None) == -1
+    assert C.LIB.cola_checks_probe(0, 8, 1 << 20, 1024, None) == -1
+    assert C.cola_strerror(-7).startswith("an index failed its bounds check")
