@@ -48,9 +48,13 @@ def outputs(nq, ng, L):
     return out
 
 
-def probe(ws):
+def probe():
     """(launch rc, status after it) of the probe hook, for indexes inside and
-    outside the checked bound n."""
+    outside the checked bound n, on the workspace of a small initialised
+    simulation (cola_init clears its status word)."""
+    sim = C.Simulation(C.make_config(8, 16, 32.0, 0.05, 1.0, 4))
+    sim.init_tables()
+    ws = sim.ws
     s = torch.cuda.current_stream().cuda_stream
     res = []
     for index, n in ((3, 8), (8, 8), (63, 64), (40, 7)):
@@ -62,7 +66,7 @@ def probe(ws):
 def child(path):
     assert C.LIB.cola_checks_enabled() == 1, "the child must load the checked build"
     out = {f"{nq}_{ng}_{k}": v for nq, ng, L in CASES for k, v in outputs(nq, ng, L).items()}
-    out["probe"] = np.array(probe(C.Simulation(C.make_config(8, 16, 32.0, 0.05, 1.0, 4)).ws))
+    out["probe"] = np.array(probe())
     np.savez(path, **out)
 
 
@@ -82,9 +86,8 @@ def checked(tmp_path_factory):
 
 def test_normal_build_has_no_checks():
     assert C.LIB.cola_checks_enabled() == 0
-    ws = C.Simulation(C.make_config(8, 16, 32.0, 0.05, 1.0, 4)).ws
     # in range: runs; out of range: refused on the host (no device check would catch it)
-    assert probe(ws) == [(0, 0), (-1, 0), (0, 0), (-1, 0)]
+    assert probe() == [(0, 0), (-1, 0), (0, 0), (-1, 0)]
 
 
 def test_checked_build_latches_a_failed_check(checked):
