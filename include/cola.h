@@ -360,6 +360,25 @@ int cola_fft_autotune(int32_t n, float* mesh, void* ws, size_t ws_bytes, void* s
  * or a B whose tile buffers exceed the shared memory of one block. */
 int cola_fft_set_tile(int32_t n, int32_t B);
 
+/* PM path of every later force computation and step in this process (Sec. 2.2;
+ * the same force either way, up to FP32 rounding order):
+ *   1: fused passes: particles binned by mesh row, the CIC deposit inside the
+ *      z r2c pass (shared-memory counts), the CIC gather inside the z c2r pass
+ *      (partial sums per particle), then the kick;
+ *   2: separate kernels: global fixed-point deposit, z r2c of the counts, the
+ *      real force mesh written by the z c2r pass, then gather + kick;
+ *   0: automatic (the default): fused unless the particles per (x, y) mesh row,
+ *      nq^3 / ng^2, exceed COLA_FUSED_MAX_PER_ROW.  The fused passes visit each
+ *      particle in four tiles; with many particles per row that costs more than
+ *      the mesh traffic it saves (measured on GB300: 512^3 on 1536^3, 57 per
+ *      row, 86 ms fused against 94 ms separate; 768^3 on 1152^3, 341 per row,
+ *      117 ms against 66 ms).
+ * The learned convolution net always takes the fused deposit (it needs delta
+ * in real space from it) and the real force mesh.  Returns COLA_EINVAL for
+ * another mode. */
+#define COLA_FUSED_MAX_PER_ROW 96
+int cola_pm_set_path(int32_t mode);
+
 /* Set the traversal order of the particle kernels (deposit, gather, fused
  * gather + kick + drift, adjoint deposit) for later launches in this process:
  * each 256-thread block takes a brick of I x J x brick_k Lagrangian sites

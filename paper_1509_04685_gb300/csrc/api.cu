@@ -110,6 +110,14 @@ static BinBufs bin_bufs(void* ws, const Layout& L) {
 }
 static float* slots_ptr(void* ws, const Layout& L) { return reinterpret_cast<float*>(wsp(ws, L.slots)); }
 
+// the PM path (cola_pm_set_path): 0 automatic, 1 fused passes, 2 separate kernels
+static int g_pm_path = 0;
+static bool fused_path(const cola_config* cfg) {
+    if (g_pm_path) return g_pm_path == 1;
+    const double per_row = (double)cfg->nq * cfg->nq * cfg->nq / ((double)cfg->ng * cfg->ng);
+    return per_row <= COLA_FUSED_MAX_PER_ROW;
+}
+
 // The PM force of Sec. 2.2 on the interleaved force mesh F (rows (ix, iy, c)
 // of P complex): the particles are binned by mesh row; the r2c pass along z
 // deposits them row tile by row tile in shared memory and transforms the rows
@@ -129,13 +137,24 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     const long long P = fft_pitch(ng), n2 = (long long)ng * ng;
     const BinBufs bb = bin_bufs(ws, L);
     const RowBins bins{bb.start, bb.sorted, bb.cic, status_ptr(ws), (long long)nq * nq * nq, ng};
-    int rc;
-    if ((rc = launch_bins(st->d, nq, ng, cfg->box, bb, status_ptr(ws), s))) return rc;
-    // the net's input keeps delta in real space (first buffer of the learned region)
-    if ((rc = fft_z_r2c_deposit(st->d, nq, bins, F, ng, cfg->box, scale, tw,
-                                learned ? reinterpret_cast<float*>(wsp(ws, L.lrn)) : nullptr, s)))
-        return rc;
     const FRow fr = force_rows(ng);
+    const bool fused = learned || fused_path(cfg);
+    int rc;
+    if (fused) {
+        if ((rc = launch_bins(st->d, nq, ng, cfg->box, bb, status_ptr(ws), s))) return rc;
+        // the net's input keeps delta in real space (first buffer of the learned region)
+        if ((rc = fft_z_r2c_deposit(st->d, nq, bins, F, ng, cfg->box, scale, tw,
+                                    learned ? reinterpret_cast<float*>(wsp(ws, L.lrn)) : nullptr, s)))
+            return rc;
+    } else {
+        // the region is shared with the bins and the 2LPT scratch: start from zero counts
+        unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+        if (cudaMemsetAsync(dep, 0, (size_t)ng * ng * ng * 8, s) != cudaSuccess) return COLA_ECUDA;
+        if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws),
+                                    s, false)))
+            return rc;
+        if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, P, n2, fr))) return rc;
+    }
     const long long XB = 1ll << fr.xbs;
     // y lines of component 0 (outer x = xb XB + xi), then of all three components (outer 3 x + c)
     if ((rc = fft_lines(F, ng, -1, tw, s, LineGeom{3 * XB * P, ng, (int)XB, 3 * XB * ng * P, 3 * P}, kKYFwd)))
@@ -147,7 +166,7 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
                           nfilt > 1 ? (float)(kmax / (nfilt - 1)) : 1.f, &psi)))
         return rc;
     if ((rc = fft_y_inverse_force(F, ng, tw, s, psi, kf))) return rc;
-    if (to_slots) return fft_z_c2r_gather(F, ng, st->d, nq, bins, slots_ptr(ws, L), cfg->box, tw, tx, s);
+    if (to_slots && fused) return fft_z_c2r_gather(F, ng, st->d, nq, bins, slots_ptr(ws, L), cfg->box, tw, tx, s);
     if ((rc = fft_z_c2r(F, ng, tw, s, nullptr, 0, 1.f, P, 3 * n2))) return rc;
     if (learned) return net_forward(cfg->net, wsp(ws, L.lrn), ng, nq, (float)green, F, s);
     return COLA_OK;
@@ -449,6 +468,12 @@ int cola_status(void* ws, size_t ws_bytes, void* stream) {
 uint64_t cola_launch_count(void) { return g_launches; }
 
 int cola_checks_enabled(void) { return kChecks ? 1 : 0; }
+
+int cola_pm_set_path(int32_t mode) {
+    if (mode < 0 || mode > 2) return COLA_EINVAL;
+    g_pm_path = mode;
+    return COLA_OK;
+}
 
 int cola_checks_probe(int32_t index, int32_t n, void* ws, size_t ws_bytes, void* stream) {
     if (!ws || ws_bytes < kHdrBytes || n < 1 || n > kProbeInts || index < 0 || index >= kProbeInts)

@@ -46,10 +46,11 @@ constexpr int kMaxTileBins = 2 * (64 + 1);  // row tiles of at most 64 rows
 // (bxy[b] >> 16, bxy[b] & 0xffff) (coord_of(b) packs them), it starts at beg[b]
 // in the sorted arrays, and pre[b] is the number of particles in the bins
 // before it.  Returns the total.  Ends synchronised.
-template <class CoordOf>
-__device__ __forceinline__ int tile_bins(const RowBins& bins, int nb, int ng, const CoordOf& coord_of, int* beg,
-                                         int* pre, int* bxy) {
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+// The group is threads tid < nthr (whole warps) synchronised by `sync`.
+template <class CoordOf, class Sync>
+__device__ __forceinline__ int tile_bins_g(const RowBins& bins, int nb, int ng, const CoordOf& coord_of, int* beg,
+                                           int* pre, int* bxy, int tid, int nthr, const Sync& sync) {
+    for (int b = tid; b < nb; b += nthr) {
         const int xy = coord_of(b);
         const int k = (xy >> 16) * ng + (xy & 0xffff);
         const int s0 = __ldg(bins.start + k), s1 = __ldg(bins.start + k + 1);
@@ -57,10 +58,10 @@ __device__ __forceinline__ int tile_bins(const RowBins& bins, int nb, int ng, co
         pre[b + 1] = s1 - s0;
         bxy[b] = xy;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    sync();
+    if (tid < 32) {
         const unsigned full = 0xffffffffu;
-        const int lane = threadIdx.x;
+        const int lane = tid;
         int carry = 0;
         for (int base = 0; base < nb; base += 32) {
             const int b = base + lane;
@@ -75,8 +76,15 @@ __device__ __forceinline__ int tile_bins(const RowBins& bins, int nb, int ng, co
         }
         if (lane == 0) pre[0] = 0;
     }
-    __syncthreads();
+    sync();
     return pre[nb];
+}
+// the whole block as the group
+template <class CoordOf>
+__device__ __forceinline__ int tile_bins(const RowBins& bins, int nb, int ng, const CoordOf& coord_of, int* beg,
+                                         int* pre, int* bxy) {
+    return tile_bins_g(bins, nb, ng, coord_of, beg, pre, bxy, (int)threadIdx.x, (int)blockDim.x,
+                       [] { __syncthreads(); });
 }
 
 // the bin holding flat index e (pre[b] <= e < pre[b + 1])
@@ -391,6 +399,175 @@ __global__ void __launch_bounds__(T, MB)
                 ahead[k] = tile_load(threadIdx.x + k * T, total, bins, beg, pre, NB);
         }
     }
+}
+
+// c2r pre-processing read straight from a row X[0..M] in global memory (the
+// same arithmetic as C2rStage)
+template <int M>
+struct C2rGlobal {
+    const float2* __restrict__ x;
+    const float2* tw;  // W_2M^k, k <= M (shared memory)
+    template <int R, int D>
+    __device__ __forceinline__ void load(int, int i0, float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = i0 + r * D;
+            float2 a = __ldg(x + k), bb = __ldg(x + M - k);
+            if (k == 0) {
+                a.y = 0.f;
+                bb.y = 0.f;
+            }
+            const float2 b = cconj(bb);
+            float2 w = tw[k];
+            w.y = -w.y;
+            const float2 d = cmul(csub(a, b), w);
+            v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
+        }
+    }
+};
+
+// c2r + gather with warp-owned rows (TX = 1): G groups of three warps per
+// block; group g takes tiles t = blockIdx.x G + g, then every gridDim.x G-th.
+// Warp c of a group transforms force component c of the tile's (x, y) row:
+// the first pass reads the row from global memory, the others run in place in
+// the warp's row buffer, separated by __syncwarp only.  The group's named
+// barrier (id g + 1, 96 threads) then lets its threads list the tile's bins
+// and gather; no block-wide barrier follows the start-up.
+template <int N, int G>
+constexpr size_t z_c2r_gather_w_smem() {
+    return ((size_t)ordered_tw_size(N / 2) + N / 2 + 1 + (size_t)G * 3 * (spad(N / 2) + 1)) * 8;
+}
+
+template <int N, int G, int MB>
+__global__ void __launch_bounds__(96 * G, MB)
+    k_fft_z_c2r_gather_w(const float2* __restrict__ data, long long rs, int ntiles, const float2* __restrict__ tw,
+                         FRow fr, long long np, RowBins bins, float* __restrict__ slots) {
+    static_assert(G >= 1 && G <= 10, "named barriers 1 .. G, at most 1024 threads");
+    constexpr int M = N / 2;
+    constexpr int NB = 4;  // 2 (TX + 1) bins
+    using Geo = WarpRow<M>;
+    extern __shared__ float2 sm[];
+    __shared__ int beg[G][NB], pre[G][NB + 1], bxy[G][NB];
+    float2* tws = sm;                        // pass-ordered twiddles of the M-point transform
+    float2* twh = tws + ordered_tw_size(M);  // W_N^k, k <= M, for the c2r pre-processing
+    float2* rows = twh + (M + 1);
+    ordered_twiddles<M, 96 * G, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += 96 * G) twh[q] = __ldg(tw + q);
+    __syncthreads();
+    const int g = threadIdx.x / 96, gl = threadIdx.x - g * 96, c = gl >> 5;
+    float2* Z = rows + (size_t)g * 3 * Geo::LSTR;
+    float2* mine = Z + c * Geo::LSTR;
+    const auto gsync = [g] { asm volatile("bar.sync %0, 96;\n" ::"r"(g + 1) : "memory"); };
+    for (int t = blockIdx.x * G + g; t < ntiles; t += gridDim.x * G) {
+        const int x = t / N, y = t - x * N;
+        sip_run<M, 32, Geo, +1, false, true>(C2rGlobal<M>{data + (frow(x, y, 0, fr) + c) * rs, twh},
+                                             SSmem<Geo>{mine}, mine, tws, NoHook());
+        // bins x0 in {x - 1, x}, y0 in {y - 1, y}; its barriers also publish the three rows
+        const int total = tile_bins_g(
+            bins, NB, N, [&](int b) { return (wrap(x - 1 + (b & 1), N) << 16) | wrap(y - 1 + (b >> 1), N); },
+            beg[g], pre[g], bxy[g], gl, 96, gsync);
+        for (int e = gl; e < total; e += 96)
+            gather_one(tile_load(e, total, bins, beg[g], pre[g], NB), bxy[g], np, N, x, 1, y, Z, Geo::LSTR, slots);
+        gsync();  // the rows and the bin list are reused by the group's next tile
+    }
+}
+
+// r2c + deposit with warp-owned rows: G groups of NR warps per block; group g
+// takes tiles t = blockIdx.x G + g, then every gridDim.x G-th (tile t is rows
+// (x, y0 .. y0 + NR - 1), t = x (N / NR) + y0 / NR, as in k_fft_z_r2c_dep_s).
+// Per tile the group clears its NR count rows and deposits the particles of
+// the tile's 2 (NR + 1) bins (integer atomics in shared memory); then warp l
+// transforms count row l in place (the first pass loads all its inputs before
+// it stores, so the complex row can overwrite the counts it came from),
+// post-processes it and writes delta_k row (x, y0 + l).  Only the group's named
+// barriers (id g + 1) separate the phases.
+template <int N, int NR, int G>
+constexpr int z_r2c_dep_w_tw() {  // float2 entries before the counts (16-byte aligned)
+    return (ordered_tw_size(N / 2) + N / 2 + 1 + 1) & ~1;
+}
+template <int N, int NR, int G>
+constexpr size_t z_r2c_dep_w_smem() {
+    return (size_t)z_r2c_dep_w_tw<N, NR, G>() * 8 + (size_t)G * NR * N * 8;
+}
+
+template <int N, int NR, int G, int MB>
+__global__ void __launch_bounds__(32 * NR * G, MB)
+    k_fft_z_r2c_dep_w(RowBins bins, float2* out, long long rs, int ntiles, float scale,
+                      const float2* __restrict__ tw, FRow fr, float* __restrict__ delta_out) {
+    constexpr int M = N / 2;
+    constexpr int TPX = N / NR;
+    constexpr int NB = 2 * (NR + 1);
+    constexpr int GT = 32 * NR;  // threads of a group
+    static_assert(NR + 1 <= N && NB <= kMaxTileBins && G * NR <= 32, "tile bins, threads per block");
+    using Geo = WarpRow<M>;
+    static_assert(Geo::LSTR <= N, "a complex row fits in its count row");
+    extern __shared__ float2 sm[];
+    __shared__ int beg[G][NB], pre[G][NB + 1], bxy[G][NB];
+    float2* tws = sm;                        // pass-ordered twiddles of the M-point transform
+    float2* twh = tws + ordered_tw_size(M);  // W_N^k, k <= M, for the r2c post-processing
+    unsigned long long* cnt_all = reinterpret_cast<unsigned long long*>(sm + z_r2c_dep_w_tw<N, NR, G>());
+    ordered_twiddles<M, GT * G, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += GT * G) twh[q] = __ldg(tw + q);
+    __syncthreads();
+    const int g = threadIdx.x / GT, gl = threadIdx.x - g * GT, l = gl >> 5, lane = gl & 31;
+    unsigned long long* cnt = cnt_all + (size_t)g * NR * N;
+    unsigned long long* myc = cnt + (size_t)l * N;
+    float2* Z = reinterpret_cast<float2*>(myc);
+    const auto gsync = [g] { asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "n"(GT) : "memory"); };
+    for (int t = blockIdx.x * G + g; t < ntiles; t += gridDim.x * G) {
+        const int x = t / TPX, y0 = (t - x * TPX) * NR;
+        ulonglong2* c2 = reinterpret_cast<ulonglong2*>(cnt);
+        for (int e = gl; e < NR * N / 2; e += GT) c2[e] = make_ulonglong2(0ull, 0ull);
+        // bins x0 in {x - 1, x}, y0' in [y0 - 1, y0 + NR - 1]; its first barrier orders the clear
+        const int total = tile_bins_g(
+            bins, NB, N,
+            [&](int b) { return (wrap(x - 1 + b / (NR + 1), N) << 16) | wrap(y0 - 1 + b % (NR + 1), N); }, beg[g],
+            pre[g], bxy[g], gl, GT, gsync);
+        for (int e = gl; e < total; e += GT)
+            deposit_one(tile_load(e, total, bins, beg[g], pre[g], NB), bxy[g], N, x, y0, NR, cnt);
+        gsync();
+        if (delta_out) {
+            float* o = delta_out + ((long long)x * N + y0 + l) * N;
+            for (int e = lane; e < N; e += 32) o[e] = (float)myc[e] * scale - 1.0f;
+        }
+        sip_run<M, 32, Geo, -1, true, true>(FixStage<N>{myc, scale}, SSmem<Geo>{Z}, Z, tws, NoHook());
+        // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / (2i)
+        float2* orow = out + frow(x, y0 + l, 0, fr) * rs;
+        for (int k = lane; k <= M; k += 32) {
+            const float2 a = Z[spad(k == M ? 0 : k)];
+            const float2 b = cconj(Z[spad(k == 0 ? 0 : M - k)]);
+            const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            const float2 D = csub(a, b);
+            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+            __stcs(orow + k, cadd(E, cmul(twh[k], O)));
+        }
+        gsync();  // the counts and the bin list are reused by the group's next tile
+    }
+}
+
+template <int N, int NR, int G, int MB>
+inline int run_z_r2c_dep_w(const RowBins& bins, float2* out, long long rs, float scale, const float2* tw, FRow fr,
+                           float* delta_out, cudaStream_t s) {
+    constexpr size_t smem = z_r2c_dep_w_smem<N, NR, G>();
+    static_assert((smem + 12 * (2 * (NR + 1)) * G + 4 * G + 1024) * MB <= 227 * 1024, "MB blocks must fit");
+    const int nt = N * (N / NR);
+    if (!set_smem((const void*)k_fft_z_r2c_dep_w<N, NR, G, MB>, smem)) return COLA_ECUDA;
+    k_fft_z_r2c_dep_w<N, NR, G, MB><<<persistent_grid(smem, (nt + G - 1) / G), 32 * NR * G, smem, s>>>(
+        bins, out, rs, nt, scale, tw, fr, delta_out);
+    return check_launch();
+}
+
+template <int N, int G, int MB>
+inline int run_z_c2r_gather_w(float2* data, long long rs, const float2* tw, FRow fr, int nq, const RowBins& bins,
+                              float* slots, cudaStream_t s) {
+    constexpr size_t smem = z_c2r_gather_w_smem<N, G>();
+    static_assert((smem + 36 * G + 1024) * MB <= 227 * 1024, "MB blocks must fit");
+    const long long np = (long long)nq * nq * nq;
+    const int nt = N * N;
+    if (!set_smem((const void*)k_fft_z_c2r_gather_w<N, G, MB>, smem)) return COLA_ECUDA;
+    k_fft_z_c2r_gather_w<N, G, MB><<<persistent_grid(smem, (nt + G - 1) / G), 96 * G, smem, s>>>(
+        data, rs, nt, tw, fr, np, bins, slots);
+    return check_launch();
 }
 
 template <int N, int NR, int T, int MB>

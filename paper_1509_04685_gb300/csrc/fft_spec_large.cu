@@ -134,9 +134,27 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
     X(1536, 1, 256, 3)      \
     X(2304, 1, 256, 2)
 
+// (n, rows per tile, groups of such tiles per block, blocks per SM) of the
+// warp-row form of the fused r2c + deposit pass; it takes precedence
+#define COLA_ZR2CDW_SPECS(X) \
+    X(1536, 4, 4, 1)
+
+// (n, groups of three warps per block, blocks per SM) of the warp-row form of
+// the fused c2r + gather pass (one x row per tile); it takes precedence
+#define COLA_ZC2RGW_SPECS(X) \
+    X(768, 8, 1)             \
+    X(1536, 8, 1)
+
 bool launch_z_r2c_dep_static(const float* d, int nq, float inv_cell, const RowBins& bins, float2* out, int n,
                              long long rs, float scale, const float2* tw, FRow fr, float* delta_out, cudaStream_t s,
                              int* rc) {
+#define COLA_CASE(NN, RR, GG, MB)                                                       \
+    if (n == NN) {                                                                      \
+        *rc = run_z_r2c_dep_w<NN, RR, GG, MB>(bins, out, rs, scale, tw, fr, delta_out, s); \
+        return true;                                                                    \
+    }
+    COLA_ZR2CDW_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, RR, TT, MB)                                                                          \
     if (n == NN) {                                                                                         \
         *rc = run_z_r2c_dep<NN, RR, TT, MB>(d, nq, inv_cell, bins, out, rs, scale, tw, fr, delta_out, s); \
@@ -149,6 +167,14 @@ bool launch_z_r2c_dep_static(const float* d, int nq, float inv_cell, const RowBi
 
 bool launch_z_c2r_gather_static(float2* data, int n, long long rs, const float2* tw, FRow fr, const float* d, int nq,
                                 float inv_cell, const RowBins& bins, float* slots, int* tx, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, GG, MB)                                                  \
+    if (n == NN) {                                                             \
+        *tx = 1;                                                               \
+        *rc = run_z_c2r_gather_w<NN, GG, MB>(data, rs, tw, fr, nq, bins, slots, s); \
+        return true;                                                           \
+    }
+    COLA_ZC2RGW_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, TX, TT, MB)                                                                       \
     if (n == NN) {                                                                                      \
         *tx = TX;                                                                                       \

@@ -20,8 +20,10 @@ namespace cola {
 // TWO: the passes read a pass-ordered twiddle table (see ordered_twiddles)
 // instead of that table: with butterflies along a line, neighbouring threads
 // have consecutive k, and W^{r k} read at stride r k N / (LS R) would hit the
-// same shared-memory banks.
-template <int NL_, bool LF_, int LSTR_, int ES_, int TWM_, bool TWO_ = false>
+// same shared-memory banks.  WARP: the tile belongs to one warp (thread index
+// = lane, passes separated by __syncwarp), so warps transform their own lines
+// without waiting for the rest of the block.
+template <int NL_, bool LF_, int LSTR_, int ES_, int TWM_, bool TWO_ = false, bool WARP_ = false>
 struct TileGeo {
     static constexpr int NL = NL_;
     static constexpr bool LF = LF_;
@@ -29,13 +31,32 @@ struct TileGeo {
     static constexpr int ES = ES_;
     static constexpr int TWM = TWM_;
     static constexpr bool TWO = TWO_;
+    static constexpr bool WARP = WARP_;
 };
+// the thread's index in the group that owns a tile, and that group's barrier
+template <class Geo>
+__device__ __forceinline__ unsigned geo_tid() {
+    if constexpr (Geo::WARP)
+        return threadIdx.x & 31u;
+    else
+        return threadIdx.x;
+}
+template <class Geo>
+__device__ __forceinline__ void geo_sync() {
+    if constexpr (Geo::WARP)
+        __syncwarp();
+    else
+        __syncthreads();
+}
 // B interleaved columns (strided y/x passes)
 template <int B>
 using ColTile = TileGeo<B, true, 1, B, 1>;
 // NR rows of the half-length complex transform of real rows of 2M values (z passes)
 template <int M, int NR>
 using RowTile = TileGeo<NR, false, spad(M) + 1, 1, 2, true>;
+// one such row owned by one warp
+template <int M>
+using WarpRow = TileGeo<1, false, spad(M) + 1, 1, 2, true, true>;
 
 // Pass-ordered twiddles: pass s (LS = product of the earlier radices, radix R)
 // reads W_{LS R}^{r k} at offset tw_offset(P, s) + (r - 1) LS + k, so that
@@ -47,6 +68,12 @@ __host__ __device__ constexpr int tw_offset(const StaticPlan& p, int s) {
         ls *= p.r[q];
     }
     return off;
+}
+__host__ __device__ constexpr bool same_plan(const StaticPlan& a, const StaticPlan& b) {
+    if (a.nr != b.nr) return false;
+    for (int i = 0; i < a.nr; ++i)
+        if (a.r[i] != b.r[i]) return false;
+    return true;
 }
 // Fill the pass-ordered table of an N-point plan in shared memory from the
 // table tw of N TWM entries exp(-2 pi i q / (N TWM)) (the same values).
@@ -106,7 +133,7 @@ __device__ __forceinline__ void spass(const In& in, const Out& out, const float2
     constexpr int TWS = N / (LS * R) * Geo::TWM;
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        const unsigned b = geo_tid<Geo>() + (unsigned)(it * T);
         if (NB % T != 0 && it == IT - 1 && b >= (unsigned)NB) break;
         int l, j;
         if constexpr (Geo::LF) {
@@ -143,10 +170,10 @@ __device__ __forceinline__ void srun_tail(float2* a, float2* b, const Out& out, 
     const float2* twp = Geo::TWO ? tw + tw_offset(P, S) : tw;
     if constexpr (S == P.nr - 1) {
         spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, twp);
-        __syncthreads();
+        geo_sync<Geo>();
     } else {
         spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{b}, twp);
-        __syncthreads();
+        geo_sync<Geo>();
         srun_tail<N, T, Geo, SIGN, S + 1>(b, a, out, tw);
     }
 }
@@ -160,7 +187,7 @@ __device__ __forceinline__ void srun_out(const In& in, const Out& out, float2* a
     constexpr StaticPlan P = static_plan(N);
     static_assert(P.ok && P.nr >= 2, "specialised transforms need two or more passes");
     spass<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
-    __syncthreads();
+    geo_sync<Geo>();
     hook();
     srun_tail<N, T, Geo, SIGN, 1>(a, b, out, tw);
 }
@@ -206,17 +233,17 @@ __device__ __forceinline__ void spass_ip(const In& in, const Out& out, const flo
     };
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        const unsigned b = geo_tid<Geo>() + (unsigned)(it * T);
         if (NB % T == 0 || it < IT - 1 || b < (unsigned)NB) {
             int l, j;
             coords(b, l, j);
             in.template load<R, NBL>(l, j, v[it]);
         }
     }
-    __syncthreads();
+    geo_sync<Geo>();
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        const unsigned b = geo_tid<Geo>() + (unsigned)(it * T);
         if (NB % T != 0 && it == IT - 1 && b >= (unsigned)NB) break;
         int l, j;
         coords(b, l, j);
@@ -243,16 +270,17 @@ __device__ __forceinline__ void sip_tail(float2* a, const Out& out, const float2
     constexpr StaticPlan P = PL::P;
     constexpr int R = P.r[S];
     constexpr int LS = plan_ls(P, S);
-    static_assert(!Geo::TWO, "pass-ordered twiddles are laid out for the default plan");
+    static_assert(!Geo::TWO || same_plan(P, static_plan(N)), "pass-ordered twiddles are laid out for the default plan");
+    const float2* twp = Geo::TWO ? tw + tw_offset(P, S) : tw;
     if constexpr (S == P.nr - 1) {
         if constexpr (LAST_IP)
-            spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
+            spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, twp);
         else
-            spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, tw);
-        __syncthreads();
+            spass<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, out, twp);
+        geo_sync<Geo>();
     } else {
-        spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{a}, tw);
-        __syncthreads();
+        spass_ip<N, T, Geo, R, LS, SIGN>(SSmem<Geo>{a}, SSmem<Geo>{a}, twp);
+        geo_sync<Geo>();
         sip_tail<N, T, Geo, SIGN, S + 1, LAST_IP, PL>(a, out, tw);
     }
 }
@@ -271,7 +299,7 @@ __device__ __forceinline__ void sip_run(const In& in, const Out& out, float2* a,
         spass_ip<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
     else
         spass<N, T, Geo, P.r[0], 1, SIGN>(in, SSmem<Geo>{a}, tw);
-    __syncthreads();
+    geo_sync<Geo>();
     hook();
     sip_tail<N, T, Geo, SIGN, 1, LAST_IP, PL>(a, out, tw);
 }

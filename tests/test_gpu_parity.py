@@ -274,6 +274,40 @@ def test_single_cola_step_vs_oracle(plin, growth):
         assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
 
 
+# (nq, ng, L): 3x, 1.5x (fractional lattice-to-mesh ratio) and 1x meshes
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("nq,ng,L", [(32, 96, 128.0), (32, 48, 128.0), (24, 24, 96.0)])
+def test_both_pm_paths_vs_oracle(path, nq, ng, L, plin, growth):
+    # fused passes (1) and separate kernels (2): force and one node against the oracle
+    tab = cm.step_table(COSMO, cm.time_nodes(0.05, 1.0, 40), growth)
+    ref = _oracle_state(9, nq, L, plin, growth, a=0.5)
+    ref["v"] = np.random.default_rng(2).standard_normal(ref["d"].shape) * 0.05
+    for key in ref:
+        ref[key] = f32(ref[key])
+    assert C.LIB.cola_pm_set_path(path) == 0
+    try:
+        sim = C.Simulation(config(nq, ng, L))
+        sim.init_tables()
+        sim.load_state(*(dev(ref[k]) for k in ("d", "v", "psi1", "psi2")))
+        got = host(sim.force(0.5))
+        j = 23
+        sim.step(j)
+        assert sim.status() == 0
+    finally:
+        C.LIB.cola_pm_set_path(0)
+    assert rel_l2(got, pm.pm_force(ref["d"], nq, ng, L, 1.5 * COSMO.omega_m / 0.5)) < 1e-5
+    o = {k: v.copy() for k, v in ref.items()}
+    ocola.cola_step(o, j, tab, nq, ng, L)
+    assert np.sqrt(np.mean((host(sim.d) - o["d"]) ** 2)) < 1e-5 * L / nq
+    assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
+
+
+def test_pm_path_setter_validates():
+    assert C.LIB.cola_pm_set_path(3) == -1
+    assert C.LIB.cola_pm_set_path(-1) == -1
+    assert C.LIB.cola_pm_set_path(0) == 0
+
+
 @pytest.mark.parametrize("node", [11, 39])
 def test_step_host_matches_device_step(node, plin, growth):
     # the host-buffer entry point copies in, runs the same node and copies back
