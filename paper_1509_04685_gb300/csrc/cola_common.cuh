@@ -584,6 +584,9 @@ int launch_twiddles(float2* tw, int n, cudaStream_t s);
 bool set_smem(const void* fn, size_t bytes);
 // persistent grid: blocks per SM from the shared-memory budget, at most ntiles
 int persistent_grid(size_t smem, int ntiles);
+// the same with at most max_per_sm blocks per SM (the launch bounds' count, when
+// registers or threads limit residency before shared memory does)
+int persistent_grid(size_t smem, int ntiles, int max_per_sm);
 // z passes: row r at base + r*rs (complex units), nrows rows
 // r2c: input row r = x n + y goes to output row frow(x, y, 0, fr) (fr = {n, 0, 1}: in place, same row)
 int fft_z_r2c(unsigned long long* dep, float2* out, int n, float scale, const float2* tw, cudaStream_t s,

@@ -678,8 +678,11 @@ static int num_sms() {
 
 // Persistent blocks: three tile buffers (prefetch + ping-pong), blocks per SM
 // from the shared-memory budget.
-int persistent_grid(size_t smem, int ntiles) {
+int persistent_grid(size_t smem, int ntiles) { return persistent_grid(smem, ntiles, 1 << 20); }
+
+int persistent_grid(size_t smem, int ntiles, int max_per_sm) {
     int per_sm = (int)((227 * 1024) / (smem + 1024));
+    if (per_sm > max_per_sm) per_sm = max_per_sm;
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms() * per_sm;
     return grid < ntiles ? grid : ntiles;

@@ -552,7 +552,7 @@ inline int run_z_r2c_dep_w(const RowBins& bins, float2* out, long long rs, float
     static_assert((smem + 12 * (2 * (NR + 1)) * G + 4 * G + 1024) * MB <= 227 * 1024, "MB blocks must fit");
     const int nt = N * (N / NR);
     if (!set_smem((const void*)k_fft_z_r2c_dep_w<N, NR, G, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_r2c_dep_w<N, NR, G, MB><<<persistent_grid(smem, (nt + G - 1) / G), 32 * NR * G, smem, s>>>(
+    k_fft_z_r2c_dep_w<N, NR, G, MB><<<persistent_grid(smem, (nt + G - 1) / G, MB), 32 * NR * G, smem, s>>>(
         bins, out, rs, nt, scale, tw, fr, delta_out);
     return check_launch();
 }
@@ -565,7 +565,7 @@ inline int run_z_c2r_gather_w(float2* data, long long rs, const float2* tw, FRow
     const long long np = (long long)nq * nq * nq;
     const int nt = N * N;
     if (!set_smem((const void*)k_fft_z_c2r_gather_w<N, G, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_c2r_gather_w<N, G, MB><<<persistent_grid(smem, (nt + G - 1) / G), 96 * G, smem, s>>>(
+    k_fft_z_c2r_gather_w<N, G, MB><<<persistent_grid(smem, (nt + G - 1) / G, MB), 96 * G, smem, s>>>(
         data, rs, nt, tw, fr, np, bins, slots);
     return check_launch();
 }
@@ -578,8 +578,8 @@ inline int run_z_r2c_dep(const float* d, int nq, float inv_cell, const RowBins& 
     const long long np = (long long)nq * nq * nq;
     const int nt = N * (N / NR);
     if (!set_smem((const void*)k_fft_z_r2c_dep_s<N, NR, T, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_r2c_dep_s<N, NR, T, MB><<<persistent_grid(smem, nt), T, smem, s>>>(d, nq, np, inv_cell, bins, out, rs, nt,
-                                                                               scale, tw, fr, delta_out);
+    k_fft_z_r2c_dep_s<N, NR, T, MB><<<persistent_grid(smem, nt, MB), T, smem, s>>>(d, nq, np, inv_cell, bins, out, rs,
+                                                                                   nt, scale, tw, fr, delta_out);
     return check_launch();
 }
 
@@ -591,8 +591,8 @@ inline int run_z_c2r_gather(float2* data, long long rs, const float2* tw, FRow f
     const long long np = (long long)nq * nq * nq;
     const int nt = (N / TX) * N;
     if (!set_smem((const void*)k_fft_z_c2r_gather_s<N, TX, T, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_c2r_gather_s<N, TX, T, MB><<<persistent_grid(smem, nt), T, smem, s>>>(data, rs, nt, tw, fr, d, nq, np,
-                                                                                  inv_cell, bins, slots);
+    k_fft_z_c2r_gather_s<N, TX, T, MB><<<persistent_grid(smem, nt, MB), T, smem, s>>>(data, rs, nt, tw, fr, d, nq,
+                                                                                      np, inv_cell, bins, slots);
     return check_launch();
 }
 

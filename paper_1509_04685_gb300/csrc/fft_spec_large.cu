@@ -24,8 +24,23 @@ namespace cola {
     X(2304, 4, 768, 2)       \
     X(2304, 2, 768, 3)
 
+// (n, B, threads) of the strided passes with two lines per thread; they take precedence
+#define COLA_STRIDED2_SPECS(X) \
+    X(1536, 8, 384)
+#define COLA_YPSI2_SPECS(X) \
+    X(1536, 8, 512)
+#define COLA_XGREEN2_SPECS(X) \
+    X(1536, 8, 384)
+
 bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, int nct, int ntiles,
                            const float2* tw, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, BB, TT)                                                \
+    if (n == NN && B == BB) {                                                \
+        *rc = run_strided2<NN, BB, TT>(data, sign, lg, nct, ntiles, tw, s); \
+        return true;                                                         \
+    }
+    COLA_STRIDED2_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, BB, TT)                                               \
     if (n == NN && B == BB) {                                               \
         *rc = run_strided<NN, BB, TT>(data, sign, lg, nct, ntiles, tw, s); \
@@ -38,6 +53,13 @@ bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, in
 
 bool launch_x_green_static(float2* F, int n, int B, int nct, int ntiles, const float2* tw, float gscale,
                            float kf, const float* filt, int nfilt, float fstep, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, BB, TT)                                                                      \
+    if (n == NN && B == BB) {                                                                      \
+        *rc = run_x_green2<NN, BB, TT>(F, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s);   \
+        return true;                                                                               \
+    }
+    COLA_XGREEN2_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, BB, TT, NBUF)                                                                  \
     if (n == NN && B == BB) {                                                                        \
         *rc = run_x_green<NN, BB, TT, NBUF>(F, nct, ntiles, tw, gscale, kf, filt, nfilt, fstep, s); \
@@ -137,6 +159,7 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
 // (n, rows per tile, groups of such tiles per block, blocks per SM) of the
 // warp-row form of the fused r2c + deposit pass; it takes precedence
 #define COLA_ZR2CDW_SPECS(X) \
+    X(768, 4, 6, 1)          \
     X(1536, 4, 4, 1)
 
 // (n, groups of three warps per block, blocks per SM) of the warp-row form of
@@ -188,6 +211,13 @@ bool launch_z_c2r_gather_static(float2* data, int n, long long rs, const float2*
 
 bool launch_y_psi_static(float2* data, int n, int B, LineGeom lg, long long comp2, int nct, int ntiles,
                          const float2* tw, float kf, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, BB, TT)                                                     \
+    if (n == NN && B == BB) {                                                     \
+        *rc = run_y_psi2<NN, BB, TT>(data, lg, comp2, nct, ntiles, tw, kf, s);   \
+        return true;                                                              \
+    }
+    COLA_YPSI2_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, BB, TT)                                                   \
     if (n == NN && B == BB) {                                                   \
         *rc = run_y_psi<NN, BB, TT>(data, lg, comp2, nct, ntiles, tw, kf, s); \

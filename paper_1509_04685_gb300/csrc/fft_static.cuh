@@ -659,6 +659,214 @@ __global__ void __launch_bounds__(T, 1) k_fft_y_psi_s(float2* data, LineGeom lg,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Column tiles with two lines per thread.  The tile is the ColTile layout (B
+// interleaved lines, element (l, i) at l + spad(i) B); a butterfly is taken for
+// the adjacent lines 2 l2 and 2 l2 + 1 at once: one 16-byte shared-memory
+// access per element pair and one twiddle for both, so a pass issues about
+// half the memory, twiddle and index instructions of the one-line form for
+// the same arithmetic.
+// ---------------------------------------------------------------------------
+template <int B>
+struct S2Smem {
+    float2* p;
+    __device__ __forceinline__ float4* at(int l2, int i) const {
+        return reinterpret_cast<float4*>(p + 2 * l2 + spad(i) * B);
+    }
+    template <int R, int D>
+    __device__ __forceinline__ void load(int l2, int i0, float2* v0, float2* v1) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 q = (D % 16 == 0) ? at(l2, i0)[r * (spad(D) * B / 2)] : *at(l2, i0 + r * D);
+            v0[r] = make_float2(q.x, q.y);
+            v1[r] = make_float2(q.z, q.w);
+        }
+    }
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l2, int i0, const float2* v0, const float2* v1) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 q = make_float4(v0[r].x, v0[r].y, v1[r].x, v1[r].y);
+            if constexpr (D % 16 == 0 || (D == 1 && 16 % R == 0))
+                at(l2, i0)[r * (spad(D) * B / 2)] = q;
+            else
+                *at(l2, i0 + r * D) = q;
+        }
+    }
+};
+
+// global column tile, two lines at a time: element i of line l at g + i S + l
+struct SCol2 {
+    float2* g;
+    long long S;
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l2, int i0, const float2* v0, const float2* v1) const {
+        float2* q = g + (long long)i0 * S + 2 * l2;
+        const long long st = (long long)D * S;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            __stcs(reinterpret_cast<float4*>(q + r * st), make_float4(v0[r].x, v0[r].y, v1[r].x, v1[r].y));
+    }
+};
+
+// One Stockham pass of radix R over the line pairs of a B-line tile (see
+// spass); butterfly b = (j, l2), consecutive threads take adjacent pairs.
+template <int N, int T, int B, int R, int LS, int SIGN, bool IP, class In, class Out>
+__device__ __forceinline__ void spass2(const In& in, const Out& out, const float2* __restrict__ tw) {
+    constexpr int NP = B / 2;
+    constexpr int NBL = N / R;
+    constexpr int NB = NBL * NP;
+    constexpr int IT = (NB + T - 1) / T;
+    constexpr int TWS = N / (LS * R);
+    constexpr int ITL = IP ? IT : 1;  // butterflies held at once
+    float2 v0[ITL][R], v1[ITL][R];
+    if constexpr (IP) {
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const unsigned b = threadIdx.x + (unsigned)(it * T);
+            if (NB % T == 0 || it < IT - 1 || b < (unsigned)NB)
+                in.template load<R, NBL>((int)(b % NP), (int)(b / NP), v0[it], v1[it]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const unsigned b = threadIdx.x + (unsigned)(it * T);
+        if (NB % T != 0 && it == IT - 1 && b >= (unsigned)NB) break;
+        const int l2 = (int)(b % NP), j = (int)(b / NP);
+        const int jq = (int)((unsigned)j / LS);
+        const int k = j - jq * LS;
+        float2* a0 = v0[IP ? it : 0];
+        float2* a1 = v1[IP ? it : 0];
+        if constexpr (!IP) in.template load<R, NBL>(l2, j, a0, a1);
+        if constexpr (LS > 1) {
+            const int step = k * TWS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * step];
+                if (SIGN > 0) w.y = -w.y;
+                a0[r] = cmul(a0[r], w);
+                a1[r] = cmul(a1[r], w);
+            }
+        }
+        SmallDft<R>::run(a0, SIGN);
+        SmallDft<R>::run(a1, SIGN);
+        out.template store<R, LS>(l2, jq * LS * R + k, a0, a1);
+    }
+}
+
+// passes S .. nr-1 in buffer a: in place, the last one into `out` (in place
+// as well when LAST_IP, i.e. `out` is a itself)
+template <int N, int T, int B, int SIGN, int S, bool LAST_IP, class PL, class Out>
+__device__ __forceinline__ void sip2_tail(float2* a, const Out& out, const float2* __restrict__ tw) {
+    constexpr StaticPlan P = PL::P;
+    constexpr int R = P.r[S];
+    constexpr int LS = plan_ls(P, S);
+    if constexpr (S == P.nr - 1) {
+        spass2<N, T, B, R, LS, SIGN, LAST_IP>(S2Smem<B>{a}, out, tw);
+        __syncthreads();
+    } else {
+        spass2<N, T, B, R, LS, SIGN, true>(S2Smem<B>{a}, S2Smem<B>{a}, tw);
+        __syncthreads();
+        sip2_tail<N, T, B, SIGN, S + 1, LAST_IP, PL>(a, out, tw);
+    }
+}
+
+// Transform of a B-line tile two lines per thread: the first pass reads `in`
+// (another buffer, or a itself when FIRST_IP) into a, then `hook`, the middle
+// passes run in place, the last writes `out` (a itself when LAST_IP).
+// Returns synchronised.
+template <int N, int T, int B, int SIGN, bool FIRST_IP = false, bool LAST_IP = false, class PL = PlanOf<N>, class In,
+          class Out, class Hook>
+__device__ __forceinline__ void sip2_run(const In& in, const Out& out, float2* a, const float2* __restrict__ tw,
+                                         const Hook& hook) {
+    constexpr StaticPlan P = PL::P;
+    static_assert(P.ok && P.nr >= 2 && B % 2 == 0, "two or more passes, line pairs");
+    spass2<N, T, B, P.r[0], 1, SIGN, FIRST_IP>(in, S2Smem<B>{a}, tw);
+    __syncthreads();
+    hook();
+    sip2_tail<N, T, B, SIGN, 1, LAST_IP, PL>(a, out, tw);
+}
+
+// the two-lines-per-thread forms of IkxLoad and SColIkz
+template <int N, int B>
+struct Ikx2Load {
+    float2* p;
+    float kf;
+    template <int R, int D>
+    __device__ __forceinline__ void load(int l2, int i0, float2* v0, float2* v1) const {
+        S2Smem<B>{p}.template load<R, D>(l2, i0, v0, v1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = i0 + r * D;
+            const float kx = (i == N / 2) ? 0.f : kf * (float)(i < N / 2 ? i : i - N);
+            v0[r] = make_float2(-kx * v0[r].y, kx * v0[r].x);
+            v1[r] = make_float2(-kx * v1[r].y, kx * v1[r].x);
+        }
+    }
+};
+
+struct SCol2Ikz {
+    float2* g;
+    long long S;
+    float kf;
+    int col0, half;
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l2, int i0, const float2* v0, const float2* v1) const {
+        const int c = col0 + 2 * l2;
+        const float k0 = (c == half) ? 0.f : kf * (float)c;
+        const float k1 = (c + 1 == half) ? 0.f : kf * (float)(c + 1);
+        float2* q = g + (long long)i0 * S + 2 * l2;
+        const long long st = (long long)D * S;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            __stcs(reinterpret_cast<float4*>(q + r * st),
+                   make_float4(-k0 * v0[r].y, k0 * v0[r].x, -k1 * v1[r].y, k1 * v1[r].x));
+    }
+};
+
+// k_fft_y_psi_s with two lines per thread
+template <int N, int B, int T>
+__global__ void __launch_bounds__(T, 1) k_fft_y_psi2_s(float2* data, LineGeom lg, long long comp2, int nct,
+                                                        int ntiles, const float2* __restrict__ tw, float kf) {
+    constexpr int TSZ = spad(N) * B;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = sm + TSZ;
+    float2* tws = A + TSZ;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    const SCol rows{nullptr, lg.S};
+    auto tile_base = [&](int t) {
+        const int o = t / nct;
+        const int ct = t - o * nct;
+        const int o1 = o / lg.o2n, o2 = o - o1 * lg.o2n;
+        return data + o1 * lg.s1 + o2 * lg.s2 + ct * B;
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) stile_prefetch<N, B, T>(stg, tile_base(t), rows);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        float2* base = tile_base(t);
+        const int col0 = (t - (t / nct) * nct) * B;
+        sip2_run<N, T, B, +1>(Ikx2Load<N, B>{stg, kf}, SCol2{base, lg.S}, A, tws, NoHook{});
+        const int tn = t + gridDim.x;
+        auto next = [&]() {
+            if (tn < ntiles) stile_prefetch<N, B, T>(stg, tile_base(tn), rows);
+        };
+        sip2_run<N, T, B, +1>(S2Smem<B>{stg}, SCol2Ikz{base + comp2, lg.S, kf, col0, N / 2}, A, tws, next);
+    }
+}
+
+template <int N, int B, int T>
+inline int run_y_psi2(float2* data, LineGeom lg, long long comp2, int nct, int ntiles, const float2* tw, float kf,
+                      cudaStream_t s) {
+    const size_t smem = ((size_t)2 * spad(N) * B + N) * 8;
+    if (!set_smem((const void*)k_fft_y_psi2_s<N, B, T>, smem)) return COLA_ECUDA;
+    k_fft_y_psi2_s<N, B, T><<<persistent_grid(smem, ntiles, 1), T, smem, s>>>(data, lg, comp2, nct, ntiles, tw, kf);
+    return check_launch();
+}
+
 template <int N, int B, int T>
 inline int run_y_psi(float2* data, LineGeom lg, long long comp2, int nct, int ntiles, const float2* tw, float kf,
                      cudaStream_t s) {
@@ -679,6 +887,138 @@ inline int run_strided(float2* data, int sign, LineGeom lg, int nct, int ntiles,
     auto kern = sign < 0 ? k_fft_strided_s<N, B, T, -1> : k_fft_strided_s<N, B, T, +1>;
     if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
     kern<<<persistent_grid(smem, ntiles), T, smem, s>>>(data, lg, nct, ntiles, tw);
+    return check_launch();
+}
+
+// k_fft_strided_s with two lines per thread
+template <int N, int B, int T, int SIGN>
+__global__ void __launch_bounds__(T, 1) k_fft_strided2_s(float2* data, LineGeom lg, int nct, int ntiles,
+                                                       const float2* __restrict__ tw) {
+    constexpr int TSZ = spad(N) * B;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = sm + TSZ;
+    float2* tws = A + TSZ;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    const SCol rows{nullptr, lg.S};
+    auto tile_base = [&](int t) {
+        const int o = t / nct;
+        const int ct = t - o * nct;
+        const int o1 = o / lg.o2n, o2 = o - o1 * lg.o2n;
+        return data + o1 * lg.s1 + o2 * lg.s2 + ct * B;
+    };
+    int t = blockIdx.x;
+    if (t < ntiles) stile_prefetch<N, B, T>(stg, tile_base(t), rows);
+    for (; t < ntiles; t += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int tn = t + gridDim.x;
+        auto next = [&]() {
+            if (tn < ntiles) stile_prefetch<N, B, T>(stg, tile_base(tn), rows);
+        };
+        sip2_run<N, T, B, SIGN>(S2Smem<B>{stg}, SCol2{tile_base(t), lg.S}, A, tws, next);
+    }
+}
+
+template <int N, int B, int T>
+inline int run_strided2(float2* data, int sign, LineGeom lg, int nct, int ntiles, const float2* tw, cudaStream_t s) {
+    constexpr size_t smem = line_pass_smem<N, B, T>();
+    auto kern = sign < 0 ? k_fft_strided2_s<N, B, T, -1> : k_fft_strided2_s<N, B, T, +1>;
+    if (!set_smem((const void*)kern, smem)) return COLA_ECUDA;
+    kern<<<persistent_grid(smem, ntiles, 1), T, smem, s>>>(data, lg, nct, ntiles, tw);
+    return check_launch();
+}
+
+// x line of one component, two lines at a time (SXIO)
+template <int N>
+struct SX2IO {
+    float2* g;
+    template <int R, int D>
+    __device__ __forceinline__ void store(int l2, int i0, const float2* v0, const float2* v1) const {
+        using G = XGeom<N>;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long o = (D % G::XB == 0) ? G::off(i0) + (long long)r * (D / G::XB) * G::SB : G::off(i0 + r * D);
+            __stcs(reinterpret_cast<float4*>(g + o + 2 * l2), make_float4(v0[r].x, v0[r].y, v1[r].x, v1[r].y));
+        }
+    }
+};
+
+// k_fft_x_green_s with two lines per thread in its transforms
+template <int N, int B, int T>
+__global__ void __launch_bounds__(T, 1) k_fft_x_green2_s(float2* F, int nct, int ntiles, const float2* __restrict__ tw,
+                                                       float gscale, float kf, const float* __restrict__ filt,
+                                                       int nfilt, float fstep) {
+    using G = XGeom<N>;
+    constexpr int TSZ = spad(N) * B;
+    constexpr int TB = T / B;    // line-element stride between a thread's spectrum values
+    constexpr int EPT = N / TB;  // spectrum values per thread
+    static_assert(T % B == 0 && N % TB == 0, "tile must split evenly over the block");
+    constexpr int half = N / 2;
+    extern __shared__ float2 sm[];
+    float2* stg = sm;
+    float2* A = sm + TSZ;
+    float2* tws = A + TSZ;
+    for (int q = threadIdx.x; q < N; q += T) tws[q] = __ldg(tw + q);
+    const int c = threadIdx.x % B;   // this thread's column in the Green phase
+    const int i0 = threadIdx.x / B;  // and its first line element: i = i0 + q TB
+    auto elem = [&](float2* base, int q) -> float2& {
+        if constexpr (TB % 16 == 0)
+            return base[c + spad(i0) * B + q * spad(TB) * B];
+        else
+            return base[c + spad(i0 + q * TB) * B];
+    };
+    auto tile_off = [&](int t) {
+        const int iy = t / nct;
+        return (long long)iy * G::RS + (long long)(t - iy * nct) * B;
+    };
+    const XOff<N> xo{};
+    int t = blockIdx.x;
+    if (t < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(t), xo);
+    for (; t < ntiles; t += gridDim.x) {
+        const int iy = t / nct;
+        const int col0 = (t - iy * nct) * B;
+        const long long off = (long long)iy * G::RS + col0;
+        cp_async_wait_all();
+        __syncthreads();
+        sip2_run<N, T, B, -1, false, true, typename GreenPlans<N>::F>(S2Smem<B>{stg}, S2Smem<B>{A}, A, tws, NoHook{});
+        const float ky = kf * (float)(iy < half ? iy : iy - N);
+        const float kz = kf * (float)(col0 + c);
+        const float kyz2 = ky * ky + kz * kz;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int i = i0 + q * TB;
+            const float kx = kf * (float)(i < half ? i : i - N);
+            const float k2 = kx * kx + kyz2;
+            float gk = k2 > 0.f ? gscale / k2 : 0.f;
+            if (filt) {
+                // radial transfer T(|k|), piecewise linear on nodes b * fstep
+                const float u = sqrtf(k2) / fstep;
+                int b = (int)u;
+                if (b > nfilt - 2) b = nfilt - 2;
+                const float f = fminf(u - (float)b, 1.f);
+                gk *= (1.f - f) * filt[b] + f * filt[b + 1];
+            }
+            float2& x = elem(A, q);
+            x = cscale(x, gk);
+        }
+        __syncthreads();
+        sip2_run<N, T, B, +1, false, false, typename GreenPlans<N>::I1>(Ikx2Load<N, B>{A, kf}, SX2IO<N>{F + off}, stg,
+                                                                        tws, NoHook{});
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) stile_prefetch<N, B, T>(stg, F + tile_off(tn), xo);
+        sip2_run<N, T, B, +1, true, false, typename GreenPlans<N>::I2>(S2Smem<B>{A}, SX2IO<N>{F + off + G::P}, A,
+                                                                       tws, NoHook{});
+    }
+}
+
+template <int N, int B, int T>
+inline int run_x_green2(float2* F, int nct, int ntiles, const float2* tw, float gscale, float kf, const float* filt,
+                        int nfilt, float fstep, cudaStream_t s) {
+    constexpr size_t smem = ((size_t)2 * spad(N) * B + N) * 8;
+    if (!set_smem((const void*)k_fft_x_green2_s<N, B, T>, smem)) return COLA_ECUDA;
+    k_fft_x_green2_s<N, B, T><<<persistent_grid(smem, ntiles, 1), T, smem, s>>>(F, nct, ntiles, tw, gscale, kf, filt,
+                                                                               nfilt, fstep);
     return check_launch();
 }
 
@@ -890,7 +1230,7 @@ inline int run_z_c2r(float2* data, long long rs, long long nrows, const float2* 
     const long long nt = (nrows + NR - 1) / NR;
     if (nt > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
     if (!set_smem((const void*)k_fft_z_c2r_s<N, NR, T, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_c2r_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt), T, smem, s>>>(data, rs, nrows, (int)nt, tw);
+    k_fft_z_c2r_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt, MB), T, smem, s>>>(data, rs, nrows, (int)nt, tw);
     return check_launch();
 }
 
@@ -902,7 +1242,7 @@ inline int run_z_r2c_fix(unsigned long long* dep, float2* out, long long rs, lon
     const long long nt = (nrows + NR - 1) / NR;
     if (nt > 0x7fffffff) return COLA_EUNSUPPORTED_SIZE;
     if (!set_smem((const void*)k_fft_z_r2c_fix_s<N, NR, T, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_r2c_fix_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt), T, smem, s>>>(dep, out, rs, nrows, (int)nt,
+    k_fft_z_r2c_fix_s<N, NR, T, MB><<<persistent_grid(smem, (int)nt, MB), T, smem, s>>>(dep, out, rs, nrows, (int)nt,
                                                                                      scale, tw, fr);
     return check_launch();
 }
