@@ -367,12 +367,15 @@ int cola_fft_set_tile(int32_t n, int32_t B);
  *      (partial sums per particle), then the kick;
  *   2: separate kernels: global fixed-point deposit, z r2c of the counts, the
  *      real force mesh written by the z c2r pass, then gather + kick;
- *   0: automatic (the default): fused unless the particles per (x, y) mesh row,
- *      nq^3 / ng^2, exceed COLA_FUSED_MAX_PER_ROW.  The fused passes visit each
- *      particle in four tiles; with many particles per row that costs more than
- *      the mesh traffic it saves (measured on GB300: 512^3 on 1536^3, 57 per
- *      row, 86 ms fused against 94 ms separate; 768^3 on 1152^3, 341 per row,
- *      117 ms against 66 ms).
+ *   0: automatic (the default): fused where the library has warp-row forms
+ *      of both fused z passes (ng = 768, 1536) and the particles per (x, y)
+ *      mesh row, nq^3 / ng^2, are at most COLA_FUSED_MAX_PER_ROW; separate
+ *      otherwise.  The fused passes visit each particle in four tiles; with
+ *      many particles per row that costs more than the mesh traffic it saves,
+ *      and the other mesh sizes' fused forms are slower than the separate
+ *      kernels (measured on GB300: 512^3 on 1536^3, 57 per row, 84 ms fused
+ *      against 87 ms separate; 768^3 on 1152^3, 341 per row, 117 ms against
+ *      66 ms; 768^3 on 2304^3 376 ms against 364 ms).
  * The learned convolution net always takes the fused deposit (it needs delta
  * in real space from it) and the real force mesh.  Returns COLA_EINVAL for
  * another mode. */

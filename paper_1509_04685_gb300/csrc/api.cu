@@ -115,7 +115,7 @@ static int g_pm_path = 0;
 static bool fused_path(const cola_config* cfg) {
     if (g_pm_path) return g_pm_path == 1;
     const double per_row = (double)cfg->nq * cfg->nq * cfg->nq / ((double)cfg->ng * cfg->ng);
-    return per_row <= COLA_FUSED_MAX_PER_ROW;
+    return fused_passes_warp_rows(cfg->ng) && per_row <= COLA_FUSED_MAX_PER_ROW;
 }
 
 // The PM force of Sec. 2.2 on the interleaved force mesh F (rows (ix, iy, c)
@@ -141,19 +141,24 @@ static int pm_mesh_forces(const cola_config* cfg, const cola_state* st, double g
     const bool fused = learned || fused_path(cfg);
     int rc;
     if (fused) {
+        if ((rc = mark_dep_dirty(ws, s))) return rc;  // the bins overwrite the fixed-point region
         if ((rc = launch_bins(st->d, nq, ng, cfg->box, bb, status_ptr(ws), s))) return rc;
         // the net's input keeps delta in real space (first buffer of the learned region)
         if ((rc = fft_z_r2c_deposit(st->d, nq, bins, F, ng, cfg->box, scale, tw,
                                     learned ? reinterpret_cast<float*>(wsp(ws, L.lrn)) : nullptr, s)))
             return rc;
     } else {
-        // the region is shared with the bins and the 2LPT scratch: start from zero counts
+        // zero counts to start from (the region is shared with the bins and the
+        // 2LPT scratch); the r2c pass leaves them zero again, and only then is
+        // the region marked clean
         unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
-        if (cudaMemsetAsync(dep, 0, (size_t)ng * ng * ng * 8, s) != cudaSuccess) return COLA_ECUDA;
+        if ((rc = clear_dep_if_dirty(ws, dep, (size_t)ng * ng * ng, s))) return rc;
+        if ((rc = mark_dep_dirty(ws, s))) return rc;
         if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, nq, ng, cfg->box, nullptr, status_ptr(ws),
                                     s, false)))
             return rc;
         if ((rc = fft_z_r2c(dep, F, ng, scale, tw, s, P, n2, fr))) return rc;
+        if ((rc = mark_dep_clean(ws, s))) return rc;
     }
     const long long XB = 1ll << fr.xbs;
     // y lines of component 0 (outer x = xb XB + xi), then of all three components (outer 3 x + c)
@@ -308,6 +313,7 @@ static int power_common(const cola_config* cfg, const cola_state* st, int32_t no
         if ((rc = launch_snapshot_coeffs(cfg, a_node, a_out, sp, s))) return rc;
         snap = sp;
     }
+    if ((rc = mark_dep_dirty(ws, s))) return rc;
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
     float2* mk = reinterpret_cast<float2*>(wsp(ws, L.F));  // plain ng_pk mesh in the force-mesh region
     const float2* tw = twiddles_for(ng_pk, cfg, ws, s, &rc);
@@ -352,6 +358,7 @@ int cola_density(const cola_config* cfg, const cola_state* st, float* delta, voi
     if (!state_ok(st, false) || !delta) return COLA_EINVAL;
     cudaStream_t s = S(stream);
     unsigned long long* dep = reinterpret_cast<unsigned long long*>(wsp(ws, L.dep));
+    if ((rc = mark_dep_dirty(ws, s))) return rc;
     if (cudaMemsetAsync(dep, 0, (size_t)cfg->ng * cfg->ng * cfg->ng * 8, s) != cudaSuccess) return COLA_ECUDA;
     if ((rc = launch_deposit_ex(st->d, nullptr, nullptr, nullptr, dep, cfg->nq, cfg->ng, cfg->box, nullptr,
                                 status_ptr(ws), s)))

@@ -473,6 +473,8 @@ constexpr size_t kHdrSigmaAmp = 64;       // double: P(k) amplitude A (sigma8 no
 constexpr size_t kHdrSnap = 128;          // 6 doubles: snapshot drift (dr, dD1, dD2), redshift-space (cv, c1, c2)
 constexpr size_t kHdrProbe = 512;         // 64 ints written by cola_checks_probe
 constexpr int kProbeInts = 64;
+constexpr size_t kHdrDepState = 768;      // int: kDepClean while the fixed-point region holds zero counts
+constexpr int kDepClean = 0x5a5a5a5a;     // (a byte pattern, so cudaMemsetAsync can write it)
 constexpr size_t kHdrFilter = 1024;       // radial filter basis table (<= 64 floats)
 constexpr size_t kHdrTable = 4096;        // kMaxSteps x kTableCols doubles
 constexpr size_t kHdrTwiddle = 262144;    // 3 slots of kMaxFft float2
@@ -583,6 +585,7 @@ int launch_twiddles(float2* tw, int n, cudaStream_t s);
 // raise a kernel's dynamic shared-memory limit (cached per kernel and size)
 bool set_smem(const void* fn, size_t bytes);
 // persistent grid: blocks per SM from the shared-memory budget, at most ntiles
+int num_sms();  // of the current device (cached)
 int persistent_grid(size_t smem, int ntiles);
 // the same with at most max_per_sm blocks per SM (the launch bounds' count, when
 // registers or threads limit residency before shared memory does)
@@ -633,6 +636,14 @@ int launch_bins(const float* d, int nq, int ng, double box, const BinBufs& b, in
 int launch_slot_kick_drift(const float* slots, const int* pos, cola_state st, const double* row, int nq, int last,
                            int pm_only, int* status, cudaStream_t s);
 int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cudaStream_t s);
+// The separate-kernel PM path deposits into the fixed-point region and its z
+// r2c pass clears the counts as it reads them, so the region stays zero from
+// one such step to the next.  Everything else that writes the region (the
+// fused path's bins, the 2LPT scratch, the P(k) and density calls) marks it
+// dirty first; clear_dep_if_dirty zeroes it only when marked.
+int mark_dep_dirty(void* ws, cudaStream_t s);
+int mark_dep_clean(void* ws, cudaStream_t s);
+int clear_dep_if_dirty(void* ws, unsigned long long* dep, size_t count, cudaStream_t s);
 // cola_checks_probe's kernel: area[index] = index if the bounds check index < n passes
 int launch_checks_probe(int* area, int index, int n, int* status, cudaStream_t s);
 
@@ -648,6 +659,8 @@ int fft_z_r2c_deposit(const float* d, int nq, const RowBins& bins, float2* F, in
 // those rows into slots; *tx receives the tile's x rows for the kick.
 int fft_z_c2r_gather(float2* F, int ng, const float* d, int nq, const RowBins& bins, float* slots, double box,
                      const float2* tw, int* tx, cudaStream_t s);
+// true when both fused z passes of an n^3 mesh have warp-row forms (fft_spec_large.cu)
+bool fused_passes_warp_rows(int n);
 // exclusive scan of a[0..n) in place, a[n] = total; sums holds scan_sums_bytes(n) (scan.cu)
 int exclusive_scan(int* a, long long n, int* sums, cudaStream_t s);
 size_t scan_sums_bytes(long long n);

@@ -667,7 +667,7 @@ static int strided_cols(int n) {
 static bool runtime_tile_fits(int n, int B) { return (size_t)(3 * spad(n) * B + n) * 8 <= 220 * 1024; }
 
 static int g_num_sms = 0;
-static int num_sms() {
+int num_sms() {
     if (!g_num_sms) {
         int dev = 0;
         cudaGetDevice(&dev);

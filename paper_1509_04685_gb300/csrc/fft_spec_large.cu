@@ -26,11 +26,20 @@ namespace cola {
 
 // (n, B, threads) of the strided passes with two lines per thread; they take precedence
 #define COLA_STRIDED2_SPECS(X) \
-    X(1536, 8, 384)
+    X(768, 16, 512)             \
+    X(1152, 8, 384)             \
+    X(1536, 8, 384)             \
+    X(2304, 4, 384)
 #define COLA_YPSI2_SPECS(X) \
-    X(1536, 8, 512)
+    X(768, 16, 512)          \
+    X(1152, 8, 384)          \
+    X(1536, 8, 512)          \
+    X(2304, 4, 384)
 #define COLA_XGREEN2_SPECS(X) \
-    X(1536, 8, 384)
+    X(768, 16, 384)            \
+    X(1152, 8, 384)            \
+    X(1536, 8, 384)            \
+    X(2304, 4, 384)
 
 bool launch_strided_static(float2* data, int n, int B, int sign, LineGeom lg, int nct, int ntiles,
                            const float2* tw, cudaStream_t s, int* rc) {
@@ -167,6 +176,17 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
 #define COLA_ZC2RGW_SPECS(X) \
     X(768, 8, 1)             \
     X(1536, 8, 1)
+
+bool fused_passes_warp_rows(int n) {
+    bool r2c = false, c2r = false;
+#define COLA_CASE(NN, ...) r2c = r2c || n == NN;
+    COLA_ZR2CDW_SPECS(COLA_CASE)
+#undef COLA_CASE
+#define COLA_CASE(NN, ...) c2r = c2r || n == NN;
+    COLA_ZC2RGW_SPECS(COLA_CASE)
+#undef COLA_CASE
+    return r2c && c2r;
+}
 
 bool launch_z_r2c_dep_static(const float* d, int nq, float inv_cell, const RowBins& bins, float2* out, int n,
                              long long rs, float scale, const float2* tw, FRow fr, float* delta_out, cudaStream_t s,

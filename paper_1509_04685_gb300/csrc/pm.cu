@@ -492,6 +492,28 @@ int launch_slot_force(const float* slots, const int* pos, float* out, int nq, cu
     return check_launch();
 }
 
+int mark_dep_dirty(void* ws, cudaStream_t s) {
+    return cudaMemsetAsync(wsp(ws, kHdrDepState), 0, sizeof(int), s) == cudaSuccess ? COLA_OK : COLA_ECUDA;
+}
+
+int mark_dep_clean(void* ws, cudaStream_t s) {
+    return cudaMemsetAsync(wsp(ws, kHdrDepState), kDepClean & 0xff, sizeof(int), s) == cudaSuccess ? COLA_OK
+                                                                                                   : COLA_ECUDA;
+}
+
+// zero count[0 .. n) (n even) unless the state word says it is already zero
+__global__ void k_clear_if_dirty(ulonglong2* __restrict__ c, long long n2, const int* state) {
+    if (*state == kDepClean) return;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += (long long)gridDim.x * blockDim.x)
+        c[e] = make_ulonglong2(0ull, 0ull);
+}
+
+int clear_dep_if_dirty(void* ws, unsigned long long* dep, size_t count, cudaStream_t s) {
+    k_clear_if_dirty<<<num_sms() * 4, 512, 0, s>>>(reinterpret_cast<ulonglong2*>(dep), (long long)(count / 2),
+                                                         reinterpret_cast<const int*>(wsp(ws, kHdrDepState)));
+    return check_launch();
+}
+
 // one thread: the bounds check of index < n, then the write it guards
 __global__ void k_checks_probe(int* area, int index, int n, int* status) {
     if (bounds_ok(status, index < n)) area[index] = index;

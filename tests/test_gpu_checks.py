@@ -4,7 +4,8 @@ It stands in for a memory checker, which cannot run here: every data-dependent
 index of the PM step (bin key, sorted position, the z cell of a CIC record) is
 checked on the device before the access it guards, and a failed check skips the
 access and latches COLA_EBOUNDS.  A child process loads that build and runs the
-tiny and odd-shape cases (2LPT set-up, PM force, two COLA nodes, density):
+tiny and odd-shape cases (2LPT set-up, PM force, two COLA nodes, density) on
+both PM paths:
 the results must be bit-identical to the normal build's and the status word
 clear.  The probe hook shows the latch itself: an index that fails its check
 leaves COLA_EBOUNDS in the status word, with the write skipped.
@@ -35,16 +36,23 @@ CASES = [(16, 48, 64.0), (10, 30, 40.0), (12, 18, 48.0), (6, 18, 30.0), (8, 12, 
          (64, 192, 192.0)]
 
 
-def outputs(nq, ng, L):
+PATHS = (1, 2)  # fused passes, separate kernels (cola_pm_set_path)
+
+
+def outputs(nq, ng, L, path):
     """2LPT set-up, PM force, two COLA nodes and the density with the library
-    this process loaded, and the status word after them."""
-    sim = C.Simulation(C.make_config(nq, ng, L, 0.05, 1.0, 40))
-    sim.ic(seed=9)
-    out = {"force": sim.force(0.05).cpu().numpy()}
-    sim.step(0)
-    sim.step(1)
-    out.update(d=sim.d.cpu().numpy(), v=sim.v.cpu().numpy(), density=sim.density().cpu().numpy(),
-               status=np.array([sim.status()]))
+    this process loaded, on one PM path, and the status word after them."""
+    assert C.LIB.cola_pm_set_path(path) == 0
+    try:
+        sim = C.Simulation(C.make_config(nq, ng, L, 0.05, 1.0, 40))
+        sim.ic(seed=9)
+        out = {"force": sim.force(0.05).cpu().numpy()}
+        sim.step(0)
+        sim.step(1)
+        out.update(d=sim.d.cpu().numpy(), v=sim.v.cpu().numpy(), density=sim.density().cpu().numpy(),
+                   status=np.array([sim.status()]))
+    finally:
+        C.LIB.cola_pm_set_path(0)
     return out
 
 
@@ -65,7 +73,7 @@ def probe():
 
 def child(path):
     assert C.LIB.cola_checks_enabled() == 1, "the child must load the checked build"
-    out = {f"{nq}_{ng}_{k}": v for nq, ng, L in CASES for k, v in outputs(nq, ng, L).items()}
+    out = {f"{nq}_{ng}_{p}_{k}": v for nq, ng, L in CASES for p in PATHS for k, v in outputs(nq, ng, L, p).items()}
     out["probe"] = np.array(probe())
     np.savez(path, **out)
 
@@ -95,9 +103,11 @@ def test_checked_build_latches_a_failed_check(checked):
     assert checked["probe"].tolist() == [[0, 0], [0, -7], [0, 0], [0, -7]]
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("nq,ng,L", CASES)
-def test_checked_build_is_bit_identical(checked, nq, ng, L):
-    ref = outputs(nq, ng, L)
+def test_checked_build_is_bit_identical(checked, nq, ng, L, path):
+    ref = outputs(nq, ng, L, path)
     assert int(ref["status"][0]) == 0
     for name in ("status", "force", "d", "v", "density"):
-        np.testing.assert_array_equal(checked[f"{nq}_{ng}_{name}"], ref[name], err_msg=f"{nq}^3 / {ng}^3 {name}")
+        np.testing.assert_array_equal(checked[f"{nq}_{ng}_{path}_{name}"], ref[name],
+                                      err_msg=f"{nq}^3 / {ng}^3 path {path} {name}")

@@ -302,6 +302,35 @@ def test_both_pm_paths_vs_oracle(path, nq, ng, L, plin, growth):
     assert rel_l2(host(sim.v) - ref["v"], o["v"] - ref["v"]) < 1e-5
 
 
+def test_separate_path_survives_other_users_of_its_mesh_region():
+    # the separate path keeps its fixed-point counts zero between steps and
+    # clears them only after another call wrote the region (the fused path's
+    # bins, P(k), density): interleaving those calls changes no result
+    nq, ng, L = 16, 48, 64.0
+
+    def run(interleave):
+        sim = C.Simulation(config(nq, ng, L))
+        sim.ic(seed=4)
+        for j in range(4):
+            assert C.LIB.cola_pm_set_path(2) == 0
+            sim.step(j)
+            if interleave:
+                sim.density()
+                sim.power(48)
+                assert C.LIB.cola_pm_set_path(1) == 0
+                sim.force(0.3)
+        C.LIB.cola_pm_set_path(0)
+        assert sim.status() == 0
+        return host(sim.d), host(sim.v)
+
+    try:
+        plain, mixed = run(False), run(True)
+    finally:
+        C.LIB.cola_pm_set_path(0)
+    np.testing.assert_array_equal(mixed[0], plain[0])
+    np.testing.assert_array_equal(mixed[1], plain[1])
+
+
 def test_pm_path_setter_validates():
     assert C.LIB.cola_pm_set_path(3) == -1
     assert C.LIB.cola_pm_set_path(-1) == -1
