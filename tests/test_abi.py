@@ -170,3 +170,11 @@ def test_checks_entry_points_without_launching():
     assert C.LIB.cola_checks_probe(0, 8, None, 1 << 20, None) == -1
     assert C.LIB.cola_checks_probe(0, 8, 1 << 20, 1024, None) == -1
     assert C.cola_strerror(-7).startswith("an index failed its bounds check")
+
+
+def test_pm_path_setter_validates_without_launching():
+    import paper_1509_04685_gb300 as C
+    for bad in (-1, 3, 100):
+        assert C.LIB.cola_pm_set_path(bad) == -1
+    for good in (1, 2, 0):
+        assert C.LIB.cola_pm_set_path(good) == 0
