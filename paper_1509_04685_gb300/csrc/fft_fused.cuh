@@ -426,48 +426,54 @@ struct C2rGlobal {
     }
 };
 
-// c2r + gather with warp-owned rows (TX = 1): G groups of three warps per
-// block; group g takes tiles t = blockIdx.x G + g, then every gridDim.x G-th.
-// Warp c of a group transforms force component c of the tile's (x, y) row:
-// the first pass reads the row from global memory, the others run in place in
-// the warp's row buffer, separated by __syncwarp only.  The group's named
-// barrier (id g + 1, 96 threads) then lets its threads list the tile's bins
-// and gather; no block-wide barrier follows the start-up.
-template <int N, int G>
+// c2r + gather with warp-owned rows: G groups of 3 TX warps per block; group g
+// takes tiles t = blockIdx.x G + g, then every gridDim.x G-th (tile t is the
+// three force components of the x rows x_first .. x_first + TX - 1 at one y,
+// t = (x_first / TX) N + y: 3 TX consecutive rows of the force mesh).  Warp w of
+// a group transforms row w of the tile: the first pass reads the row from
+// global memory, the others run in place in the warp's row buffer, separated
+// by __syncwarp only.  The group's named barrier (id g + 1, 96 TX threads) then
+// lets its threads list the tile's bins and gather; no block-wide barrier
+// follows the start-up.
+template <int N, int TX, int G>
 constexpr size_t z_c2r_gather_w_smem() {
-    return ((size_t)ordered_tw_size(N / 2) + N / 2 + 1 + (size_t)G * 3 * (spad(N / 2) + 1)) * 8;
+    return ((size_t)ordered_tw_size(N / 2) + N / 2 + 1 + (size_t)G * 3 * TX * (spad(N / 2) + 1)) * 8;
 }
 
-template <int N, int G, int MB>
-__global__ void __launch_bounds__(96 * G, MB)
+template <int N, int TX, int G, int MB>
+__global__ void __launch_bounds__(96 * TX * G, MB)
     k_fft_z_c2r_gather_w(const float2* __restrict__ data, long long rs, int ntiles, const float2* __restrict__ tw,
                          FRow fr, long long np, RowBins bins, float* __restrict__ slots) {
-    static_assert(G >= 1 && G <= 10, "named barriers 1 .. G, at most 1024 threads");
+    static_assert(G >= 1 && G <= 15 && 96 * TX * G <= 1024, "named barriers 1 .. G, at most 1024 threads");
     constexpr int M = N / 2;
-    constexpr int NB = 4;  // 2 (TX + 1) bins
+    constexpr int NB = 2 * (TX + 1);
+    constexpr int GT = 96 * TX;  // threads of a group
     using Geo = WarpRow<M>;
     extern __shared__ float2 sm[];
     __shared__ int beg[G][NB], pre[G][NB + 1], bxy[G][NB];
     float2* tws = sm;                        // pass-ordered twiddles of the M-point transform
     float2* twh = tws + ordered_tw_size(M);  // W_N^k, k <= M, for the c2r pre-processing
     float2* rows = twh + (M + 1);
-    ordered_twiddles<M, 96 * G, 2>(tws, tw);
-    for (int q = threadIdx.x; q <= M; q += 96 * G) twh[q] = __ldg(tw + q);
+    ordered_twiddles<M, GT * G, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += GT * G) twh[q] = __ldg(tw + q);
     __syncthreads();
-    const int g = threadIdx.x / 96, gl = threadIdx.x - g * 96, c = gl >> 5;
-    float2* Z = rows + (size_t)g * 3 * Geo::LSTR;
-    float2* mine = Z + c * Geo::LSTR;
-    const auto gsync = [g] { asm volatile("bar.sync %0, 96;\n" ::"r"(g + 1) : "memory"); };
+    const int g = threadIdx.x / GT, gl = threadIdx.x - g * GT, w = gl >> 5;
+    float2* Z = rows + (size_t)g * 3 * TX * Geo::LSTR;
+    float2* mine = Z + w * Geo::LSTR;
+    const auto gsync = [g] { asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "n"(GT) : "memory"); };
     for (int t = blockIdx.x * G + g; t < ntiles; t += gridDim.x * G) {
-        const int x = t / N, y = t - x * N;
-        sip_run<M, 32, Geo, +1, false, true>(C2rGlobal<M>{data + (frow(x, y, 0, fr) + c) * rs, twh},
+        const int xg = t / N, y = t - xg * N, x_first = xg * TX;
+        sip_run<M, 32, Geo, +1, false, true>(C2rGlobal<M>{data + (frow(x_first, y, 0, fr) + w) * rs, twh},
                                              SSmem<Geo>{mine}, mine, tws, NoHook());
-        // bins x0 in {x - 1, x}, y0 in {y - 1, y}; its barriers also publish the three rows
+        // bins x0 in [x_first - 1, x_first + TX - 1], y0 in {y - 1, y}; its barriers
+        // also publish the rows
         const int total = tile_bins_g(
-            bins, NB, N, [&](int b) { return (wrap(x - 1 + (b & 1), N) << 16) | wrap(y - 1 + (b >> 1), N); },
-            beg[g], pre[g], bxy[g], gl, 96, gsync);
-        for (int e = gl; e < total; e += 96)
-            gather_one(tile_load(e, total, bins, beg[g], pre[g], NB), bxy[g], np, N, x, 1, y, Z, Geo::LSTR, slots);
+            bins, NB, N,
+            [&](int b) { return (wrap(x_first - 1 + b % (TX + 1), N) << 16) | wrap(y - 1 + b / (TX + 1), N); },
+            beg[g], pre[g], bxy[g], gl, GT, gsync);
+        for (int e = gl; e < total; e += GT)
+            gather_one(tile_load(e, total, bins, beg[g], pre[g], NB), bxy[g], np, N, x_first, TX, y, Z, Geo::LSTR,
+                       slots);
         gsync();  // the rows and the bin list are reused by the group's next tile
     }
 }
@@ -557,15 +563,15 @@ inline int run_z_r2c_dep_w(const RowBins& bins, float2* out, long long rs, float
     return check_launch();
 }
 
-template <int N, int G, int MB>
+template <int N, int TX, int G, int MB>
 inline int run_z_c2r_gather_w(float2* data, long long rs, const float2* tw, FRow fr, int nq, const RowBins& bins,
                               float* slots, cudaStream_t s) {
-    constexpr size_t smem = z_c2r_gather_w_smem<N, G>();
-    static_assert((smem + 36 * G + 1024) * MB <= 227 * 1024, "MB blocks must fit");
+    constexpr size_t smem = z_c2r_gather_w_smem<N, TX, G>();
+    static_assert((smem + 12 * (2 * TX + 3) * G + 1024) * MB <= 227 * 1024, "MB blocks must fit");
     const long long np = (long long)nq * nq * nq;
-    const int nt = N * N;
-    if (!set_smem((const void*)k_fft_z_c2r_gather_w<N, G, MB>, smem)) return COLA_ECUDA;
-    k_fft_z_c2r_gather_w<N, G, MB><<<persistent_grid(smem, (nt + G - 1) / G, MB), 96 * G, smem, s>>>(
+    const int nt = (N / TX) * N;
+    if (!set_smem((const void*)k_fft_z_c2r_gather_w<N, TX, G, MB>, smem)) return COLA_ECUDA;
+    k_fft_z_c2r_gather_w<N, TX, G, MB><<<persistent_grid(smem, (nt + G - 1) / G, MB), 96 * TX * G, smem, s>>>(
         data, rs, nt, tw, fr, np, bins, slots);
     return check_launch();
 }

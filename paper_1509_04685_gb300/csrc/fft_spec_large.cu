@@ -171,11 +171,11 @@ bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long l
     X(768, 4, 6, 1)          \
     X(1536, 4, 4, 1)
 
-// (n, groups of three warps per block, blocks per SM) of the warp-row form of
-// the fused c2r + gather pass (one x row per tile); it takes precedence
+// (n, x rows per tile, groups of such tiles per block, blocks per SM) of the
+// warp-row form of the fused c2r + gather pass; it takes precedence
 #define COLA_ZC2RGW_SPECS(X) \
-    X(768, 8, 1)             \
-    X(1536, 8, 1)
+    X(768, 1, 8, 1)          \
+    X(1536, 1, 8, 1)
 
 bool fused_passes_warp_rows(int n) {
     bool r2c = false, c2r = false;
@@ -210,11 +210,11 @@ bool launch_z_r2c_dep_static(const float* d, int nq, float inv_cell, const RowBi
 
 bool launch_z_c2r_gather_static(float2* data, int n, long long rs, const float2* tw, FRow fr, const float* d, int nq,
                                 float inv_cell, const RowBins& bins, float* slots, int* tx, cudaStream_t s, int* rc) {
-#define COLA_CASE(NN, GG, MB)                                                  \
-    if (n == NN) {                                                             \
-        *tx = 1;                                                               \
-        *rc = run_z_c2r_gather_w<NN, GG, MB>(data, rs, tw, fr, nq, bins, slots, s); \
-        return true;                                                           \
+#define COLA_CASE(NN, TX, GG, MB)                                                   \
+    if (n == NN) {                                                                  \
+        *tx = TX;                                                                   \
+        *rc = run_z_c2r_gather_w<NN, TX, GG, MB>(data, rs, tw, fr, nq, bins, slots, s); \
+        return true;                                                                \
     }
     COLA_ZC2RGW_SPECS(COLA_CASE)
 #undef COLA_CASE
