@@ -164,14 +164,12 @@ int cola_step(const cola_config* cfg, cola_state* st, int32_t step, void* ws, si
  * host->d, v, psi1, psi2 (each 3 Nq^3 float32, SoA, HOST pointers; pinned memory
  * gives asynchronous DMA) into the device state dev (DEVICE pointers, same
  * layout), runs node `step` exactly as cola_step does, and copies dev->d and
- * dev->v back into host->d and host->v.  The copies are spread over `stream`
- * and three internal streams (which start after the work already queued on
- * `stream`), so that several copy engines share the host link: the three
- * position components first, after which the force computation starts on
- * `stream`; v, psi1 and psi2 meanwhile, one per internal stream, and the kick
- * waits for them; d and v back on two streams at once.  The call returns
- * after the copies back have completed, so the host arrays hold the new state
- * on return.  Arguments are validated before any copy
+ * dev->v back into host->d and host->v.  The positions are copied on `stream`,
+ * where the force computation starts at once; v, psi1 and psi2 are copied on
+ * an internal stream meanwhile (it starts after the work already queued on
+ * `stream`), and the kick waits for them.  The copies back are on `stream`;
+ * the call returns after they have completed, so the host arrays hold the new
+ * state on return.  Arguments are validated before any copy
  * (COLA_EINVAL, COLA_EWORKSPACE, or a config error); if the step itself fails,
  * dev holds the copied-in state and host is unchanged.  COLA_ECUDA on a failed
  * copy or synchronisation. */
