@@ -367,16 +367,7 @@ __global__ void k_bin_count(const float* __restrict__ d, int nq, int ng, float i
         return;
     }
     key[p] = k;
-    // one atomic per distinct key of the warp (a warp's sites share one or a few
-    // (x, y) rows): the lowest lane of each key group adds the group's size,
-    // the others take consecutive ranks after it in lane order
-    const unsigned grp = __match_any_sync(__activemask(), k);
-    const int lead = __ffs(grp) - 1;
-    const unsigned lane = threadIdx.x & 31u;
-    int base = 0;
-    if (lane == (unsigned)lead) base = atomicAdd(count + k, __popc(grp));
-    base = __shfl_sync(grp, base, lead);
-    rank[p] = base + __popc(grp & ((1u << lane) - 1u));
+    rank[p] = atomicAdd(count + k, 1);
 }
 
 __global__ void k_bin_scatter(const float* __restrict__ d, int nq, int ng, float inv_cell, long long np,
