@@ -662,6 +662,8 @@ def main():
         return
     w = WORKLOADS[args.workload]
     cfg = C.make_config(w["nq"], w["ng"], w["box"], A_INIT, 1.0, N_NODES)
+    import ctypes
+    pm_path = {1: "fused", 2: "separate"}.get(C.LIB.cola_pm_path(ctypes.byref(cfg)), "unknown")
     sim = C.Simulation(cfg, device=f"cuda:{local}")
     sim.ic(seed=replica_seed(rank))
     for j in range(args.warmup):
@@ -673,7 +675,6 @@ def main():
     time.sleep(0.3)
     nk = C.LIB.cola_num_kernel_ids()
     launches0 = C.cola_launch_count()
-    import ctypes
     C.LIB.cola_profile_start(args.steps * 16 + 64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -793,7 +794,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "nq": w["nq"], "ng": w["ng"], "box": w["box"], "n_steps": N_NODES,
-                       "z_init": 1 / A_INIT - 1, "parallelism": f"replicas{world}",
+                       "z_init": 1 / A_INIT - 1, "parallelism": f"replicas{world}", "pm_path": pm_path,
                        "l2": "inputs larger than L2 (every mesh >> 129 MB); no flush"},
             "clocks": clk,
             "gpu_launches": launches,

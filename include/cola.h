@@ -382,6 +382,11 @@ int cola_fft_set_tile(int32_t n, int32_t B);
 #define COLA_FUSED_MAX_PER_ROW 96
 int cola_pm_set_path(int32_t mode);
 
+/* The PM path the next force computation or step of cfg takes under the
+ * current mode: 1 (fused passes) or 2 (separate kernels); COLA_EINVAL (or a
+ * config error) if cfg is invalid.  Host only: no launch, no device access. */
+int cola_pm_path(const cola_config* cfg);
+
 /* Set the traversal order of the particle kernels (deposit, gather, fused
  * gather + kick + drift, adjoint deposit) for later launches in this process:
  * each 256-thread block takes a brick of I x J x brick_k Lagrangian sites

@@ -115,6 +115,7 @@ def _load():
         "cola_checks_enabled": ([], ctypes.c_int),
         "cola_checks_probe": ([i32, i32, vp, sz, vp], ctypes.c_int),
         "cola_pm_set_path": ([i32], ctypes.c_int),
+        "cola_pm_path": ([cfgp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

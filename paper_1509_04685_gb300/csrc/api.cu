@@ -482,6 +482,13 @@ int cola_pm_set_path(int32_t mode) {
     return COLA_OK;
 }
 
+int cola_pm_path(const cola_config* cfg) {
+    size_t need = 0;
+    const int rc = cola_workspace_size(cfg, &need);  // validates cfg
+    if (rc) return rc;
+    return (net_on(cfg) || fused_path(cfg)) ? 1 : 2;
+}
+
 int cola_checks_probe(int32_t index, int32_t n, void* ws, size_t ws_bytes, void* stream) {
     if (!ws || ws_bytes < kHdrBytes || n < 1 || n > kProbeInts || index < 0 || index >= kProbeInts)
         return COLA_EINVAL;

@@ -178,3 +178,24 @@ def test_pm_path_setter_validates_without_launching():
         assert C.LIB.cola_pm_set_path(bad) == -1
     for good in (1, 2, 0):
         assert C.LIB.cola_pm_set_path(good) == 0
+
+
+def test_pm_path_rule_without_launching():
+    # automatic choice: fused where both fused z passes have warp-row forms (768,
+    # 1536) and nq^3 / ng^2 <= 96; separate otherwise; a forced mode wins
+    import paper_1509_04685_gb300 as C
+    byref = ctypes.byref
+    cases = {(512, 1536, 1536.0): 1, (256, 768, 768.0): 1, (768, 2304, 1536.0): 2, (768, 1152, 1536.0): 2,
+             (384, 1152, 1152.0): 2, (256, 256, 512.0): 2, (32, 96, 128.0): 2, (1536, 1536, 1536.0): 2}
+    try:
+        assert C.LIB.cola_pm_set_path(0) == 0
+        for (nq, ng, L), want in cases.items():
+            cfg = C.make_config(nq, ng, L, 0.05)
+            assert C.LIB.cola_pm_path(byref(cfg)) == want, (nq, ng)
+        cfg = C.make_config(32, 96, 128.0, 0.05)
+        for mode in (1, 2):
+            assert C.LIB.cola_pm_set_path(mode) == 0
+            assert C.LIB.cola_pm_path(byref(cfg)) == mode
+        assert C.LIB.cola_pm_path(byref(C.make_config(32, 97, 128.0, 0.05))) == -3
+    finally:
+        C.LIB.cola_pm_set_path(0)
