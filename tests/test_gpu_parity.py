@@ -504,6 +504,34 @@ def test_pm_only_run_vs_oracle(plin, growth):
     assert np.max(np.abs(p[sel] / pr[sel] - 1)) <= 1e-3
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_nonfinite_position_in_a_step(path, plin, growth):
+    # one particle with a NaN position: the step latches COLA_ENONFINITE, leaves
+    # that particle's state as it was and moves every other particle to finite values
+    nq, ng, L = 16, 48, 64.0
+    st = _oracle_state(2, nq, L, plin, growth, a=0.3)
+    d = f32(st["d"])
+    d[0, 123] = np.nan
+    v = f32(np.random.default_rng(5).standard_normal(d.shape) * 0.05)
+    assert C.LIB.cola_pm_set_path(path) == 0
+    try:
+        sim = C.Simulation(config(nq, ng, L))
+        sim.init_tables()
+        sim.load_state(dev(d), dev(v), dev(f32(st["psi1"])), dev(f32(st["psi2"])))
+        sim.step(12)
+        status = sim.status()
+    finally:
+        C.LIB.cola_pm_set_path(0)
+    assert status == -6
+    dn, vn = host(sim.d), host(sim.v)
+    assert np.isnan(dn[0, 123])
+    np.testing.assert_array_equal(vn[:, 123], v[:, 123])
+    others = np.ones(nq**3, bool)
+    others[123] = False
+    assert np.isfinite(dn[:, others]).all() and np.isfinite(vn[:, others]).all()
+    assert np.abs(vn[:, others] - v[:, others]).max() > 0
+
+
 def test_nonfinite_input_sets_status():
     nq, ng, L = 8, 24, 32.0
     sim = C.Simulation(config(nq, ng, L))
