@@ -401,31 +401,6 @@ __global__ void __launch_bounds__(T, MB)
     }
 }
 
-// c2r pre-processing read straight from a row X[0..M] in global memory (the
-// same arithmetic as C2rStage)
-template <int M>
-struct C2rGlobal {
-    const float2* __restrict__ x;
-    const float2* tw;  // W_2M^k, k <= M (shared memory)
-    template <int R, int D>
-    __device__ __forceinline__ void load(int, int i0, float2* v) const {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int k = i0 + r * D;
-            float2 a = __ldg(x + k), bb = __ldg(x + M - k);
-            if (k == 0) {
-                a.y = 0.f;
-                bb.y = 0.f;
-            }
-            const float2 b = cconj(bb);
-            float2 w = tw[k];
-            w.y = -w.y;
-            const float2 d = cmul(csub(a, b), w);
-            v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
-        }
-    }
-};
-
 // c2r + gather with warp-owned rows: G groups of 3 TX warps per block; group g
 // takes tiles t = blockIdx.x G + g, then every gridDim.x G-th (tile t is the
 // three force components of the x rows x_first .. x_first + TX - 1 at one y,

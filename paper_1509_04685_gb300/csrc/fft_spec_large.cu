@@ -121,8 +121,27 @@ bool static_tile_ok(int n, int B) {
     X(1536, 4, 256, 2)       \
     X(2304, 2, 256, 2)
 
+// (n, warps per block, blocks per SM) of the warp-row r2c of the fixed-point
+// counts; it takes precedence.  (A warp-row plain c2r was slower than the block
+// tile at 2304: 74 ms against 64 ms.)
+#define COLA_ZWARP_SPECS(X) \
+    X(2304, 16, 1)
+
+template <int N, int W, int MB>
+static int run_z_r2c_fix_w(unsigned long long* dep, float2* out, long long rs, long long nrows, float scale,
+                           const float2* tw, FRow fr, cudaStream_t s) {
+    constexpr size_t smem = z_warp_smem<N, W>();
+    static_assert((smem + 1024) * MB <= 227 * 1024, "MB blocks must fit");
+    if (!set_smem((const void*)k_fft_z_r2c_fix_w<N, W, MB>, smem)) return COLA_ECUDA;
+    const long long units = (nrows + W - 1) / W;
+    k_fft_z_r2c_fix_w<N, W, MB><<<persistent_grid(smem, (int)(units < 0x7fffffff ? units : 0x7fffffff), MB),
+                                  32 * W, smem, s>>>(dep, out, rs, nrows, scale, tw, fr);
+    return check_launch();
+}
+
 bool launch_z_c2r_static(float2* data, int n, long long rs, long long nrows, const float2* tw, cudaStream_t s,
                          int* rc) {
+
 #define COLA_CASE(NN, RR, TT, MB)                                \
     if (n == NN) {                                               \
         *rc = run_z_c2r<NN, RR, TT, MB>(data, rs, nrows, tw, s); \
@@ -135,6 +154,13 @@ bool launch_z_c2r_static(float2* data, int n, long long rs, long long nrows, con
 
 bool launch_z_r2c_fix_static(unsigned long long* dep, float2* out, int n, long long rs, long long nrows,
                              float scale, const float2* tw, FRow fr, cudaStream_t s, int* rc) {
+#define COLA_CASE(NN, WW, MB)                                                               \
+    if (n == NN && nrows == (long long)NN * NN) {                                          \
+        *rc = run_z_r2c_fix_w<NN, WW, MB>(dep, out, rs, nrows, scale, tw, fr, s);           \
+        return true;                                                                        \
+    }
+    COLA_ZWARP_SPECS(COLA_CASE)
+#undef COLA_CASE
 #define COLA_CASE(NN, RR, TT, MB)                                                   \
     if (n == NN) {                                                                  \
         *rc = run_z_r2c_fix<NN, RR, TT, MB>(dep, out, rs, nrows, scale, tw, fr, s); \

@@ -1103,6 +1103,94 @@ struct FixStage {
 // entries of the pass-ordered twiddle table of an M-point plan
 constexpr int ordered_tw_size(int M) { return tw_offset(static_plan(M), static_plan(M).nr); }
 
+// c2r pre-processing read straight from a row X[0..M] in global memory (the
+// same arithmetic as C2rStage)
+template <int M>
+struct C2rGlobal {
+    const float2* __restrict__ x;
+    const float2* tw;  // W_2M^k, k <= M (shared memory)
+    template <int R, int D>
+    __device__ __forceinline__ void load(int, int i0, float2* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int k = i0 + r * D;
+            float2 a = __ldg(x + k), bb = __ldg(x + M - k);
+            if (k == 0) {
+                a.y = 0.f;
+                bb.y = 0.f;
+            }
+            const float2 b = cconj(bb);
+            float2 w = tw[k];
+            w.y = -w.y;
+            const float2 d = cmul(csub(a, b), w);
+            v[r] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
+        }
+    }
+};
+
+// counts read straight from a row of the fixed-point mesh in global memory
+// and cleared as they are read (each pair is read once, by the first pass):
+// packed complex pairs of delta = count scale - 1, as FixStage
+template <int N>
+struct FixGlobal {
+    unsigned long long* row;
+    float scale;
+    template <int R, int D>
+    __device__ __forceinline__ void load(int, int i0, float2* v) const {
+        ulonglong2* x = reinterpret_cast<ulonglong2*>(row);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const ulonglong2 c = __ldcs(x + i0 + r * D);
+            __stcs(x + i0 + r * D, make_ulonglong2(0ull, 0ull));
+            v[r] = make_float2((float)c.x * scale - 1.0f, (float)c.y * scale - 1.0f);
+        }
+    }
+};
+
+// Plain z pass with warp-owned rows (the separate path's r2c of the counts):
+// W warps per block, warp w of block b takes rows b W + w, then every
+// gridDim.x W-th; the first pass reads the row from global memory, the others
+// run in place in the warp's row buffer with __syncwarp between them; no block
+// barrier after the start-up.
+template <int N, int W>
+constexpr size_t z_warp_smem() {
+    return ((size_t)ordered_tw_size(N / 2) + N / 2 + 1 + (size_t)W * (spad(N / 2) + 1)) * 8;
+}
+
+// forward r2c along z of the fixed-point counts (cleared as they are read):
+// input row r = x N + y, output row frow(x, y, 0, fr)
+template <int N, int W, int MB>
+__global__ void __launch_bounds__(32 * W, MB) k_fft_z_r2c_fix_w(unsigned long long* __restrict__ dep, float2* out,
+                                                               long long rs, long long nrows, float scale,
+                                                               const float2* __restrict__ tw, FRow fr) {
+    constexpr int M = N / 2;
+    using Geo = WarpRow<M>;
+    extern __shared__ float2 sm[];
+    float2* tws = sm;
+    float2* twh = tws + ordered_tw_size(M);
+    float2* rows = twh + (M + 1);
+    ordered_twiddles<M, 32 * W, 2>(tws, tw);
+    for (int q = threadIdx.x; q <= M; q += 32 * W) twh[q] = __ldg(tw + q);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* Z = rows + w * Geo::LSTR;
+    for (long long r = (long long)blockIdx.x * W + w; r < nrows; r += (long long)gridDim.x * W) {
+        const int x = (int)(r / N), y = (int)(r - (long long)x * N);
+        sip_run<M, 32, Geo, -1, false, true>(FixGlobal<N>{dep + r * N, scale}, SSmem<Geo>{Z}, Z, tws, NoHook());
+        // X[k] = E[k] + W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / (2i)
+        float2* orow = out + frow(x, y, 0, fr) * rs;
+        for (int k = lane; k <= M; k += 32) {
+            const float2 a = Z[spad(k == M ? 0 : k)];
+            const float2 b = cconj(Z[spad(k == 0 ? 0 : M - k)]);
+            const float2 E = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            const float2 D = csub(a, b);
+            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+            __stcs(orow + k, cadd(E, cmul(twh[k], O)));
+        }
+        __syncwarp();  // the row buffer is reused by the next row
+    }
+}
+
 template <int N, int NR, int T>
 constexpr size_t z_c2r_smem() {
     return ((size_t)NR * (N / 2 + 2) + 2 * (size_t)NR * (spad(N / 2) + 1) + ordered_tw_size(N / 2) + N / 2 + 1) * 8;
