@@ -122,8 +122,9 @@ bool static_tile_ok(int n, int B) {
     X(2304, 2, 256, 2)
 
 // (n, warps per block, blocks per SM) of the warp-row r2c of the fixed-point
-// counts; it takes precedence.  (A warp-row plain c2r was slower than the block
-// tile at 2304: 74 ms against 64 ms.)
+// counts; it takes precedence.  (At 1152 it was slower than the block tile,
+// 6.6 ms against 5.8 ms, and a warp-row plain c2r was slower at 2304, 74 ms
+// against 64 ms.)
 #define COLA_ZWARP_SPECS(X) \
     X(2304, 16, 1)
 
